@@ -1,0 +1,402 @@
+"""Pins for the FP64 oracle: it is checked against things other than itself.
+
+  * worked examples of Eq. 1 derived by hand (tests/golden/eq1_worked_examples.json);
+  * the force as minus the gradient of the pair potential
+    V(delta) = kappa delta^2/2 - (2/3) gamma sqrt(R) delta^(3/2), whose derivative
+    in delta is Eq. 1's magnitude (an independent route to the same numbers);
+  * Newton's third law, rotation/permutation/scaling invariance;
+  * brute-force pair search as the definition of the kd-tree search;
+  * the uniform grid's completeness condition (Sec. IV-A): every contact pair
+    lies in adjacent boxes;
+  * the adjoint against FP64 central finite differences of the forward.
+
+Plausible mistakes planted in the oracle (on the CPU) must trip at least one pin
+(test_planted_mistakes_are_caught).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import mech as M
+from paper_2105_00039_gb300 import populations as P
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "eq1_worked_examples.json")
+
+
+def _golden():
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+# ------------------------------------------------------------------ pin checks
+def check_worked_examples():
+    g = _golden()
+    prm = O.Params(**g["params"])
+    worst = 0.0
+    for case in g["cases"]:
+        st = np.array(case["state"], dtype=np.float64)
+        r = O.step(st, prm, method="brute")
+        worst = max(worst, float(np.abs(r["F"] - np.array(case["F"])).max()))
+        if "u" in case:
+            # the oracle uses the FP32 value of density 0.02 (2e-8 relative off)
+            u = np.array(case["u"])
+            rel = float(np.abs(r["u"] - u).max() / np.abs(u).max())
+            worst = max(worst, 0.0 if rel < 1e-7 else rel)
+    return worst
+
+
+def _potential(pos, diam, prm):
+    """Total pair potential; F = -grad E reproduces Eq. 1."""
+    rad = 0.5 * diam
+    I, J = O.pairs_bruteforce(pos, rad, prm.contact_margin)
+    keep = I < J
+    I, J = I[keep], J[keep]
+    d = np.linalg.norm(pos[I] - pos[J], axis=1)
+    delta = rad[I] + rad[J] + 2 * prm.contact_margin - d
+    R = rad[I] * rad[J] / (rad[I] + rad[J])
+    return float(np.sum(prm.k * delta ** 2 / 2 - (2.0 / 3.0) * prm.gamma * np.sqrt(R) * delta ** 1.5))
+
+
+def _safe_cluster(n=24, seed=3, margin=0.0, side=None):
+    """Random cluster with no pair within 2e-3 of the contact boundary."""
+    for s in range(seed, seed + 200):
+        side = side or 2.2 * n ** (1 / 3) * 5.0
+        st = P.uniform_cube(n, side, 8.0, 12.0, s).astype(np.float64)
+        pos, rad = st[:, :3], 0.5 * st[:, 3]
+        d = np.linalg.norm(pos[:, None] - pos[None], axis=2)
+        gap = rad[:, None] + rad[None] + 2 * margin - d
+        np.fill_diagonal(gap, 1.0)
+        if np.min(np.abs(gap)) > 2e-3 and (gap > 0).sum() >= n:
+            return st
+    raise RuntimeError("no safe cluster")
+
+
+def check_potential_gradient(prm=O.Params(), n=24, seed=3):
+    st = _safe_cluster(n, seed, prm.contact_margin)
+    pos, diam = st[:, :3].copy(), st[:, 3]
+    F = O.step(st, prm, method="brute")["F"]
+    h = 1e-6
+    G = np.zeros_like(pos)
+    for i in range(n):
+        for a in range(3):
+            pp = pos.copy(); pp[i, a] += h
+            pm = pos.copy(); pm[i, a] -= h
+            G[i, a] = -(_potential(pp, diam, prm) - _potential(pm, diam, prm)) / (2 * h)
+    return float(np.abs(G - F).max() / max(np.abs(F).max(), 1e-12))
+
+
+def check_newton3(state, prm=O.Params()):
+    r = O.step(state, prm)
+    return float(np.abs(r["F"].sum(0)).max() / max(np.abs(r["F"]).sum(), 1e-300))
+
+
+def check_pairs_methods_agree(state, margin=0.0):
+    pos, rad = state[:, :3].astype(np.float64), 0.5 * state[:, 3].astype(np.float64)
+    a = O.pairs_bruteforce(pos, rad, margin)
+    b = O.pairs_kdtree(pos, rad, margin)
+    return len(a[0]) == len(b[0]) and (a[0] == b[0]).all() and (a[1] == b[1]).all()
+
+
+def check_grid_completeness(state32, margin=0.0):
+    g = O.grid(state32, margin)
+    pos, rad = state32[:, :3].astype(np.float64), 0.5 * state32[:, 3].astype(np.float64)
+    I, J = O.pairs_bruteforce(pos, rad, margin)
+    b = g["box"]
+    ok = True
+    ok &= bool(np.all(np.abs(b[I] - b[J]) <= 1))
+    ok &= bool(np.all(b >= 1)) and bool(np.all(b <= g["dims"] - 2))
+    ok &= int(g["start"][-1]) == len(state32)
+    ok &= bool(np.all(np.diff(g["key"][g["perm"]]) >= 0))
+    # each agent inside its box, allowing the FP32 rounding of (p - o)/e
+    o = g["origin"].astype(np.float64)
+    e = float(g["edge"])
+    lo = o + b * e
+    ok &= bool(np.all(pos >= lo - 1e-4 * e)) and bool(np.all(pos < lo + e + 1e-4 * e))
+    return ok
+
+
+# ------------------------------------------------------------------ tests
+def test_worked_examples():
+    assert check_worked_examples() < 1e-12
+
+
+def test_force_is_minus_potential_gradient():
+    assert check_potential_gradient() < 1e-7
+
+
+def test_force_is_minus_potential_gradient_with_margin_and_constants():
+    assert check_potential_gradient(O.Params(k=2.5, gamma=1.2, contact_margin=0.75), n=20, seed=11) < 1e-7
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_newton_third_law(seed):
+    assert check_newton3(P.small_uniform(seed)) < 1e-13
+
+
+def test_non_overlapping_contribute_nothing():
+    st = P.jittered_lattice(64, 4, 13.0, 0.4, 8.0, 12.0, seed=2)   # gaps >= 13 - 0.8 - 12 > 0
+    r = O.step(st, O.Params())
+    assert len(r["I"]) == 0 and np.all(r["F"] == 0) and np.all(r["u"] == 0)
+
+
+def test_self_pair_and_coincident_centres():
+    st = np.array([[1, 2, 3, 10], [1, 2, 3, 10], [8, 2, 3, 10]], dtype=np.float32)
+    r = O.step(st, O.Params(), method="brute")
+    pairs = set(zip(r["I"].tolist(), r["J"].tolist()))
+    assert pairs == {(0, 2), (2, 0), (1, 2), (2, 1)}   # coincident pair (0, 1) excluded
+    assert np.all(np.isfinite(r["F"]))
+
+
+def test_rotation_and_axis_permutation_invariance():
+    st = P.small_uniform(4)[:1500].astype(np.float64)
+    r0 = O.step(st, O.Params())
+    perm = [2, 0, 1]
+    st2 = st.copy(); st2[:, :3] = st[:, perm]
+    r1 = O.step(st2, O.Params())
+    assert np.array_equal(r0["I"], r1["I"])
+    np.testing.assert_allclose(r1["F"], r0["F"][:, perm], rtol=0, atol=1e-12)
+    th = 0.7
+    Q = np.array([[math.cos(th), -math.sin(th), 0], [math.sin(th), math.cos(th), 0], [0, 0, 1]])
+    st3 = st.copy(); st3[:, :3] = st[:, :3] @ Q.T
+    r3 = O.step(st3, O.Params(), pairs=(r0["I"], r0["J"]))
+    np.testing.assert_allclose(r3["F"], r0["F"] @ Q.T, rtol=0, atol=1e-10)
+
+
+def test_input_permutation_invariance():
+    st = P.small_uniform(5)[:2000]
+    rng = np.random.default_rng(0)
+    q = rng.permutation(len(st))
+    r0 = O.step(st, O.Params())
+    r1 = O.step(st[q], O.Params())
+    np.testing.assert_allclose(r1["F"], r0["F"][q], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(r1["u"], r0["u"][q], rtol=0, atol=1e-13)
+
+
+def test_length_scaling():
+    # phi(lambda delta; lambda R) = lambda phi: all lengths x2 doubles F
+    st = P.small_uniform(6)[:1000].astype(np.float64)
+    r0 = O.step(st, O.Params())
+    r1 = O.step(2 * st, O.Params())
+    np.testing.assert_allclose(r1["F"], 2 * r0["F"], rtol=0, atol=1e-11)
+
+
+@pytest.mark.parametrize("kind", ["uniform", "lattice", "clustered"])
+def test_kdtree_equals_bruteforce(kind):
+    if kind == "uniform":
+        st = P.small_uniform(7)
+    elif kind == "lattice":
+        st = P.jittered_lattice(4096, 16, 9.0, 1.5, 9.0, 11.0, 7)
+    else:
+        st = P.uniform_cube(3000, 60.0, 8.0, 12.0, 7)      # ~50 neighbours each
+    assert check_pairs_methods_agree(st)
+    assert check_pairs_methods_agree(st, margin=1.5)
+
+
+def test_pair_count_small_lattice():
+    # 2x2x2 lattice, spacing 9, d = 10: each agent touches its 3 face neighbours
+    st = P.jittered_lattice(8, 2, 9.0, 0.0, 10.0, 10.0, 0)
+    I, J = O.pairs_bruteforce(st[:, :3].astype(float), 0.5 * st[:, 3].astype(float))
+    assert len(I) == 24
+
+
+def test_grid_hand_example():
+    st = np.array([[0, 0, 0, 10], [25, 0, 0, 10]], dtype=np.float32)
+    g = O.grid(st)
+    assert g["edge"] == 10 and np.array_equal(g["origin"], [-10, -10, -10])
+    assert list(g["dims"]) == [5, 3, 3]
+    assert list(g["key"]) == [21, 23] and g["nboxes"] == 45
+    assert g["start"][21] == 0 and g["start"][22] == 1 and g["start"][24] == 2
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_grid_completeness(seed):
+    assert check_grid_completeness(P.small_uniform(seed))
+    assert check_grid_completeness(P.jittered_lattice(4096, 16, 9.0, 1.5, 9.0, 11.0, seed), 1.5)
+    assert check_grid_completeness(P.uniform_cube(2000, 40.0, 8.0, 12.0, seed))
+
+
+def test_grid_negative_and_tiny_extent():
+    st = np.array([[-5.5, -100, 3, 9], [-5.25, -100, 3, 11]], dtype=np.float32)
+    assert check_grid_completeness(st)
+    g = O.grid(st)
+    assert list(g["dims"]) == [3, 3, 3]
+
+
+def test_displacement_rules():
+    prm = O.Params(k=1.0, gamma=0.0, adherence=0.5, max_disp=3.0)
+    st = np.array([[0, 0, 0, 10], [9.5, 0, 0, 10]], dtype=np.float64)   # delta = 0.5, |F| = 0.5
+    r = O.step(st, prm, method="brute")
+    assert np.all(r["Fn"] == 0.5) and not r["moving"].any()            # strict >
+    r = O.step(st, O.Params(k=1.0, gamma=0.0, adherence=0.4999, max_disp=3.0), method="brute")
+    assert r["moving"].all()
+    # cap: |v| = 6.4645/10.47 = 0.617 > 0.5 -> |u| = 0.5, direction kept
+    st = np.array([[0, 0, 0, 10], [0, 5, 0, 10]], dtype=np.float64)
+    r = O.step(st, O.Params(max_disp=0.5), method="brute")
+    np.testing.assert_allclose(np.linalg.norm(r["u"], axis=1), 0.5, rtol=1e-15)
+    np.testing.assert_allclose(r["u"][0] / 0.5, [0, -1, 0], atol=1e-15)
+    r = O.step(st, O.Params(max_disp=0.7), method="brute")
+    assert not r["capped"].any()
+    # freeze (benchmark B rule): max displacement 0
+    r = O.step(P.small_uniform(0), O.Params(max_disp=0.0))
+    assert np.all(r["u"] == 0)
+
+
+def test_mass_scaling_of_displacement():
+    # same force, diameter doubled -> displacement / 8 (m ~ d^3)
+    prm = O.Params(k=1.0, gamma=0.0, adherence=0.0)
+    a = O.step(np.array([[0, 0, 0, 10], [9, 0, 0, 10]], float), prm, method="brute")
+    # a sphere of d=20 against a d=0.0 ... use a contact with the same delta
+    b = O.step(np.array([[0, 0, 0, 20], [14, 0, 0, 10]], float), prm, method="brute")
+    assert a["F"][0, 0] == b["F"][0, 0] == -1.0
+    np.testing.assert_allclose(b["u"][0, 0] * 8, a["u"][0, 0], rtol=1e-14)
+
+
+# ------------------------------------------------------------------ adjoint pins
+def _fd_fixture(seed=5, n=27, steps=3):
+    """A 3x3x3 jittered lattice whose trajectory keeps every piecewise test
+    (adherence, cap, contact onset) far from its boundary."""
+    for s in range(seed, seed + 300):
+        st = P.jittered_lattice(n, 3, 9.0, 1.5, 9.0, 11.0, s).astype(np.float64)
+        prm = O.Params(adherence=0.05, max_disp=0.045)
+        _, recs = O.trajectory(st, prm, steps, "brute", keep=True)
+        ok = True
+        for rec in recs:
+            mg = O.margins(rec, prm)
+            pos, rad = rec["state"][:, :3], 0.5 * rec["state"][:, 3]
+            d = np.linalg.norm(pos[:, None] - pos[None], axis=2)
+            gap = rad[:, None] + rad[None] - d
+            np.fill_diagonal(gap, 1.0)
+            ok &= mg["adherence"].min() > 1e-4 and mg["cap"].min() > 1e-4
+            ok &= np.abs(gap).min() > 2e-3
+        if ok and any(r["capped"].any() for r in recs) and any((~r["moving"]).any() for r in recs):
+            return st, prm
+    raise RuntimeError("no FD-safe fixture")
+
+
+def check_adjoint_fd(steps=3):
+    st, prm = _fd_fixture(steps=steps)
+    n = len(st)
+    target = st[:, :3] + 0.3 * np.sin(np.arange(3 * n).reshape(n, 3))
+    res = O.trajectory_grad(st, target, prm, steps, "brute")
+    h = 1e-6
+    errs = []
+
+    def L(state=st, p=prm):
+        return O.trajectory_loss(state, target, p, steps, "brute")
+
+    for name, key in (("k", "dk"), ("gamma", "dgamma")):
+        pp = O.Params(**{**prm.__dict__}); setattr(pp, name, getattr(prm, name) + h)
+        pm = O.Params(**{**prm.__dict__}); setattr(pm, name, getattr(prm, name) - h)
+        # the oracle rounds params to FP32; perturb in FP64 by bypassing that
+        fd = (_loss64(st, target, pp, steps) - _loss64(st, target, pm, steps)) / (2 * h)
+        errs.append(abs(fd - res[key]) / max(abs(fd), 1e-12))
+    rng = np.random.default_rng(1)
+    for _ in range(3):
+        dirn = np.zeros_like(st)
+        dirn[:, :3] = rng.standard_normal((n, 3))
+        dirn[:, 3] = 0.3 * rng.standard_normal(n)
+        fd = (L(st + h * dirn) - L(st - h * dirn)) / (2 * h)
+        an = float(np.sum(res["dpos"] * dirn[:, :3]) + np.sum(res["ddiam"] * dirn[:, 3]))
+        errs.append(abs(fd - an) / max(abs(fd), 1e-12))
+    return max(errs)
+
+
+def _loss64(st, target, prm, steps):
+    """Loss with parameters used at full FP64 (no FP32 rounding), for FD in k, gamma."""
+    orig = M.Params.as64
+    try:
+        M.Params.as64 = lambda self: self
+        return O.trajectory_loss(st, target, prm, steps, "brute")
+    finally:
+        M.Params.as64 = orig
+
+
+def test_adjoint_matches_central_differences():
+    orig = M.Params.as64
+    try:
+        M.Params.as64 = lambda self: self      # FD in FP64 parameters on both sides
+        assert check_adjoint_fd() < 1e-6
+    finally:
+        M.Params.as64 = orig
+
+
+# ------------------------------------------------------------------ planted mistakes
+def _plant(monkeypatch, which):
+    orig_terms = M.pair_terms
+    orig_disp = M.displacement
+    orig_grad = M.trajectory_grad
+
+    if which == "drop_gamma":
+        def terms(pos, diam, prm, I, J):
+            t = orig_terms(pos, diam, prm, I, J)
+            t["phi"] = prm.k * t["delta"]
+            return t
+        monkeypatch.setattr(M, "pair_terms", terms)
+    elif which == "wrong_sign":
+        def terms(pos, diam, prm, I, J):
+            t = orig_terms(pos, diam, prm, I, J)
+            t["u"] = -t["u"]
+            return t
+        monkeypatch.setattr(M, "pair_terms", terms)
+    elif which == "diameter_as_radius":
+        def terms(pos, diam, prm, I, J):
+            return orig_terms(pos, 2.0 * diam, prm, I, J)
+        monkeypatch.setattr(M, "pair_terms", terms)
+    elif which == "R_sum":
+        def terms(pos, diam, prm, I, J):
+            t = orig_terms(pos, diam, prm, I, J)
+            r = 0.5 * diam
+            R = r[I] + r[J]
+            t["root"] = np.sqrt(R * t["delta"])
+            t["phi"] = prm.k * t["delta"] - prm.gamma * t["root"]
+            return t
+        monkeypatch.setattr(M, "pair_terms", terms)
+    elif which == "transposed_index":
+        def terms(pos, diam, prm, I, J):
+            return orig_terms(pos, diam, prm, J, I)
+        monkeypatch.setattr(M, "pair_terms", terms)
+    elif which == "adherence_ge":
+        def disp(F, diam, prm):
+            r = orig_disp(F, diam, prm)
+            mv = r["Fn"] >= prm.adherence
+            r["moving"] = mv
+            r["u"] = np.where(mv[:, None], r["v"], 0.0)
+            return r
+        monkeypatch.setattr(M, "displacement", disp)
+
+
+def _pins_pass(which):
+    g_ok = check_worked_examples() < 1e-12
+    p_ok = check_potential_gradient(n=16, seed=3) < 1e-7
+    n_ok = check_newton3(P.small_uniform(0)[:1500]) < 1e-13
+    d_ok = True
+    if which == "adherence_ge":
+        prm = O.Params(k=1.0, gamma=0.0, adherence=0.5)
+        r = M.step(np.array([[0, 0, 0, 10], [9.5, 0, 0, 10]], float), prm, method="brute")
+        d_ok = not r["moving"].any()
+    return g_ok and p_ok and n_ok and d_ok
+
+
+@pytest.mark.parametrize("which", ["drop_gamma", "wrong_sign", "diameter_as_radius", "R_sum",
+                                   "transposed_index", "adherence_ge"])
+def test_planted_mistakes_are_caught(monkeypatch, which):
+    assert _pins_pass("none")
+    _plant(monkeypatch, which)
+    assert not _pins_pass(which)
+
+
+def test_planted_adjoint_mistake_is_caught(monkeypatch):
+    orig = M.trajectory_grad
+
+    def bad(*a, **k):
+        r = orig(*a, **k)
+        r["dk"] = -r["dk"]
+        return r
+    monkeypatch.setattr(M.Params, "as64", lambda self: self)
+    assert check_adjoint_fd() < 1e-6
+    monkeypatch.setattr(O, "trajectory_grad", bad)
+    assert check_adjoint_fd() > 1e-3
