@@ -1,0 +1,315 @@
+#!/usr/bin/env python
+"""Throughput of the mechanical-interaction step (agent-steps/s).
+
+Workload: 2^20 cells on a jittered 102^3 lattice (spacing 9, jitter +-1.5,
+diameters U[9, 11]), 100 fused steps with the grid rebuilt every step.  One
+bench step = those 100 steps from the same initial rows, so a bench step
+processes 2^20 * 100 agent-steps.  Before each timed step a 256 MB buffer is
+written to flush the 129 MB L2 (outside the step's CUDA events).
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 oracle on the
+host cores on a bounded sample of the same workload instead.
+
+Multi-GPU: the path is weak-scaled as independent replicas (each rank runs its
+own population; no collective on the data path); the barrier and the max over
+ranks only frame the timing.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+N_LATTICE = 1 << 20
+SIM_STEPS = 100
+BYTES_PER_AGENT_SWEEP = 32          # sweep + move: read 16 B row, write 16 B row
+BYTES_PER_AGENT_STEP = 88           # whole step (grid bin 16, scatter 40, sweep 32)
+BYTES_PER_BOX = 12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def reduce_max(pg, value: float, device=None) -> float:
+    """Max of a per-rank float over all ranks (identity without a process group)."""
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples taken while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(state, nsteps_sample: int):
+    """The FP64 oracle as it stands, one full step of the whole population per
+    sample step; returns (agent-steps/s, seconds)."""
+    import oracle as O
+    t0 = time.perf_counter()
+    st = state
+    for _ in range(nsteps_sample):
+        st = O.step(st, O.Params())["state"]
+    dt = time.perf_counter() - t0
+    return len(state) * nsteps_sample / dt, dt
+
+
+def run_reference(args, world, rank, pg):
+    from paper_2105_00039_gb300 import populations as P
+    if rank != 0:
+        return
+    st = P.lattice_1m(0)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(st, 1)
+    times = []
+    for _ in range(args.steps):
+        _, dt = cpu_oracle_rate(st, 1)
+        times.append(dt)
+    total = sum(times)
+    value = len(st) * args.steps / total
+    line = {
+        "impl": "reference", "metric": "agent-steps/s", "value": value, "unit": "agent-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "lattice_1m: 2^20 cells, 102^3 lattice spacing 9 jitter 1.5, d U[9,11]",
+                   "n_agents": len(st), "sample": "1 oracle step of the full population per bench step",
+                   "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "agent-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": "1 FP64 oracle step (cKDTree pair search + numpy Eq. 1) of all 2^20 cells per bench step"},
+        "e2e": {"value": value, "unit": "agent-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local, pg):
+    import torch
+
+    from paper_2105_00039_gb300 import populations as P
+    from paper_2105_00039_gb300 import ugmech as U
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    st = P.lattice_1m(seed=rank)
+    n = len(st)
+    prm = U.Params()
+    x0 = torch.from_numpy(st).to(dev)
+    x = torch.empty_like(x0)
+    max_boxes = U.estimate_max_boxes(x0, prm.contact_margin, slack=1.5)
+    sp = U.Stepper(n, max_boxes, dev)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    nev = 2 + 5 * SIM_STEPS
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    lib = U.load()
+    stream = torch.cuda.current_stream()
+
+    def reset():
+        x.copy_(x0)
+        U._check(lib.ug_iota(U._ptr(perm), n, U._stream()), "ug_iota")
+
+    # warm-up (also creates the CUDA handles of the trace events)
+    events = [torch.cuda.Event(enable_timing=True) for _ in range(nev)]
+    for e in events:
+        e.record(stream)
+    for _ in range(args.warmup):
+        reset()
+        sp.step(x, perm, prm, SIM_STEPS)
+    sp.check("warm-up")
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kern_ms = {k: 0.0 for k in ("bounds", "key", "scan", "place", "canon", "sweep")}
+    names = ["key", "scan", "place", "canon", "sweep"]
+    if pg is not None:
+        pg.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            reset()
+            sp.step_traced(x, perm, prm, SIM_STEPS, events)
+            ends[k].record(stream)
+            ends[k].synchronize()
+            kern_ms["bounds"] += events[0].elapsed_time(events[1])
+            for t in range(SIM_STEPS):
+                for j, nm in enumerate(names):
+                    kern_ms[nm] += events[1 + 5 * t + j].elapsed_time(events[2 + 5 * t + j])
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if pg is not None:
+        pg.barrier()
+    sp.check("timed steps")
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    tot_ms = reduce_max(pg, sum(step_ms), dev)
+    ms_per_step = tot_ms / args.steps
+    value = world * n * SIM_STEPS * args.steps / (tot_ms / 1000.0)
+
+    # roofline of the dominant kernel (time-weighted, per launch)
+    launches = {"bounds": args.steps, **{nm: args.steps * SIM_STEPS for nm in names}}
+    dom = max(kern_ms, key=kern_ms.get)
+    avg_launch_ms = kern_ms[dom] / launches[dom]
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        peaks = json.load(f)
+    hbm = float(peaks["hbm_gbs"])
+    alg_bytes = {"sweep": BYTES_PER_AGENT_SWEEP * n, "canon": 48 * n, "key": 24 * n,
+                 "place": 16 * n, "scan": 12 * max_boxes, "bounds": 16 * n}[dom]
+    achieved = alg_bytes / (avg_launch_ms / 1000.0) / 1e9
+    # whole-step HBM roofline (algorithmic bytes of the method per step)
+    step_alg = (BYTES_PER_AGENT_STEP * n + BYTES_PER_BOX * max_boxes / 1.5) * SIM_STEPS
+    step_gbs = step_alg / (ms_per_step / 1000.0) / 1e9
+
+    line = {
+        "metric": "agent-steps/s", "value": value, "unit": "agent-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "lattice_1m: 2^20 cells, 102^3 lattice spacing 9 jitter 1.5, d U[9,11]; "
+                               "100 fused steps (grid rebuilt each step) per bench step",
+                   "n_agents": n, "sim_steps_per_step": SIM_STEPS, "max_boxes": max_boxes,
+                   "l2": "flushed (256 MB write) before each timed step, outside its events",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                     "avg_launch_us": avg_launch_ms * 1000.0,
+                     "alg_bytes_per_launch": alg_bytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                     "step_alg_gbs": step_gbs, "step_frac": step_gbs / hbm},
+        "kernel_ms_share": {k: v / sum(kern_ms.values()) for k, v in kern_ms.items()},
+        "gpu_launches": args.steps * (2 + 5 * SIM_STEPS),
+        "clocks": clk.summary(),
+        "wall_s_timed_region": wall,
+    }
+
+    # end to end through the public API: pinned host rows in, rows (by id) out
+    if not args.no_e2e:
+        sim = U.Simulation(n, max_boxes, dev)
+        host_in = torch.from_numpy(st).pin_memory()
+        host_out = torch.empty((n, 4), dtype=torch.float32).pin_memory()
+        for _ in range(2):
+            sim.run(host_in, prm, SIM_STEPS, host_out)
+        torch.cuda.synchronize()
+        e_ms = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sim.run(host_in, prm, SIM_STEPS, host_out)
+            b.record(stream)
+            b.synchronize()
+            e_ms += a.elapsed_time(b)
+        sim.stepper.check("e2e")
+        e_ms = reduce_max(pg, e_ms, dev)
+        line["e2e"] = {"value": world * n * SIM_STEPS * args.steps / (e_ms / 1000.0),
+                       "unit": "agent-steps/s", "h2d_bytes_per_step": 16 * n,
+                       "d2h_bytes_per_step": 16 * n}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, secs = cpu_oracle_rate(st, 3)
+        line["cpu_baseline"] = {"value": rate, "unit": "agent-steps/s", "cores": 1, "kind": "oracle",
+                                "sample": f"3 FP64 oracle steps of all 2^20 cells ({secs:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local, pg = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank, pg)
+        else:
+            run_ours(args, world, rank, local, pg)
+    finally:
+        if pg is not None:
+            pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

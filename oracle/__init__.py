@@ -5,8 +5,8 @@ legs may import this package.  It shares no code with the CUDA library.
 """
 from .mech import (Params, grid, pairs_bruteforce, pairs_kdtree, find_pairs, pair_terms,
                    forces, mass, displacement, step, trajectory, trajectory_grad,
-                   trajectory_loss, mse_loss, margins)
+                   trajectory_loss, mse_loss, margins, step_sampled)
 
 __all__ = ["Params", "grid", "pairs_bruteforce", "pairs_kdtree", "find_pairs", "pair_terms",
            "forces", "mass", "displacement", "step", "trajectory", "trajectory_grad",
-           "trajectory_loss", "mse_loss", "margins"]
+           "trajectory_loss", "mse_loss", "margins", "step_sampled"]

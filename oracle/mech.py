@@ -153,7 +153,7 @@ def pairs_kdtree(pos: np.ndarray, rad: np.ndarray, margin: float = 0.0
 
 def find_pairs(pos, rad, margin=0.0, method="auto"):
     if method == "auto":
-        method = "brute" if len(pos) <= 6000 else "kdtree"
+        method = "brute" if len(pos) <= 1500 else "kdtree"
     if method == "brute":
         return pairs_bruteforce(pos, rad, margin)
     return pairs_kdtree(pos, rad, margin)
@@ -235,6 +235,39 @@ def trajectory(state0, prm: Params = Params(), nsteps: int = 1, method="auto",
             recs.append(dict(state=st, **{k: v for k, v in r.items() if k != "state"}))
         st = r["state"]
     return (st, recs) if keep else st
+
+
+# --------------------------------------------------------------------- sampled form
+def step_sampled(state, idx, prm: Params = Params()):
+    """The step's F, S, contact count and displacement for the rows in `idx`
+    only, each against every row (agent by agent, for populations too large
+    for `step`).  Candidates come from a cKDTree ball query, the contact test
+    and Eq. 1 are the same FP64 expressions as in `pair_terms`."""
+    from scipy.spatial import cKDTree
+
+    prm64 = prm.as64()
+    st = np.asarray(state, dtype=np.float64)
+    pos, diam = st[:, :3], st[:, 3]
+    rad = 0.5 * diam
+    idx = np.asarray(idx, dtype=np.int64)
+    rmax = 2.0 * float(rad.max()) + 2.0 * prm64.contact_margin
+    lists = cKDTree(pos).query_ball_point(pos[idx], r=rmax * (1.0 + 1e-9) + 1e-12)
+    I = np.concatenate([np.full(len(l), k, np.int64) for k, l in enumerate(lists)]) if len(idx) else np.zeros(0, np.int64)
+    J = np.concatenate([np.asarray(l, np.int64) for l in lists]) if len(idx) else np.zeros(0, np.int64)
+    gi = idx[I]
+    keep = gi != J
+    gi, J, I = gi[keep], J[keep], I[keep]
+    delta, d = _contact_test(pos[gi], pos[J], rad[gi], rad[J], prm64.contact_margin)
+    keep = (delta > 0.0) & (d > 0.0)
+    gi, J, I = gi[keep], J[keep], I[keep]
+    t = pair_terms(pos, diam, prm64, gi, J)
+    f = t["phi"][:, None] * t["u"]
+    m = len(idx)
+    F = np.stack([np.bincount(I, weights=f[:, c], minlength=m) for c in range(3)], axis=1)
+    S = np.bincount(I, weights=prm64.k * t["delta"] + prm64.gamma * t["root"], minlength=m)
+    npairs = np.bincount(I, minlength=m)
+    disp = displacement(F, diam[idx], prm64)
+    return dict(F=F, S=S, npairs=npairs, I=idx[I], J=J, delta=t["delta"], **disp)
 
 
 # --------------------------------------------------------------------- adjoint

@@ -1,0 +1,381 @@
+// C ABI entry points (include/ugmech.h): argument checks, workspace layout and
+// the per-step kernel sequence.  All device work is asynchronous on the
+// caller's stream; nothing here allocates device memory.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <utility>
+
+#include "ug_internal.cuh"
+
+namespace ug {
+
+static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int device_sm_count() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 148;
+    if (dev < 64 && cached[dev] > 0) return cached[dev];
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+        sms = 148;
+    if (dev < 64) cached[dev] = sms;
+    return sms;
+}
+
+static uint32_t bounds_copies(uint32_t nsims) { return nsims == 1 ? kBoundsCopiesSingle : 1u; }
+
+// Layout (base may be null to size only).  The first three regions (ctrl,
+// counts, bounds) are contiguous and are the only ones that need zeroing.
+size_t layout_workspace(void *base, uint32_t n, uint32_t nsims, uint32_t max_boxes, Workspace *w) {
+    size_t off = 0;
+    char *b = static_cast<char *>(base);
+    auto take = [&](size_t bytes) -> char * {
+        char *p = b ? b + off : nullptr;
+        off = align256(off + bytes);
+        return p;
+    };
+    w->ctrl = reinterpret_cast<Ctrl *>(take(sizeof(Ctrl)));
+    w->counts = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (size_t)max_boxes));
+    w->bounds = reinterpret_cast<uint32_t *>(
+        take(sizeof(uint32_t) * kBoundsWords * (size_t)bounds_copies(nsims) * nsims));
+    const size_t zero_end = off;
+    w->start = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * ((size_t)max_boxes + 1)));
+    w->key = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (size_t)n));
+    w->rank = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (size_t)n));
+    w->tmp = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (size_t)n));
+    w->sorted = reinterpret_cast<float4 *>(take(sizeof(float4) * (size_t)n));
+    w->perm2 = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (size_t)n));
+    w->geo = reinterpret_cast<ug_grid_info *>(take(sizeof(ug_grid_info) * (size_t)nsims));
+    w->ntiles = std::max<uint32_t>(1u, (uint32_t)(((size_t)max_boxes + kScanTile - 1) / kScanTile));
+    w->scan_status = reinterpret_cast<unsigned long long *>(take(8 * (size_t)w->ntiles));
+    w->bytes = off;
+    (void)zero_end;
+    return off;
+}
+
+static size_t zero_bytes(const Workspace &w) {
+    return (size_t)(reinterpret_cast<char *>(w.start) - reinterpret_cast<char *>(w.ctrl));
+}
+
+static int cuda_status(cudaError_t e) { return e == cudaSuccess ? UG_OK : UG_ECUDA; }
+static int last_launch() { return cuda_status(cudaGetLastError()); }
+
+int run_steps(float4 *state, uint32_t *perm, const SimArgs &sa, int nsteps, uint32_t max_boxes,
+              const Workspace &w, int sweep_block, const StepSaves *saves, int32_t *status,
+              cudaStream_t s, cudaEvent_t const *events) {
+    const uint32_t n = sa.n;
+    auto mark = [&](int k) {
+        if (events) cudaEventRecord(events[k], s);
+    };
+    if (cudaMemsetAsync(w.ctrl, 0, zero_bytes(w), s) != cudaSuccess) return UG_ECUDA;
+    mark(0);
+    launch_bounds(state, sa, w, w.geo, max_boxes, status, s);
+    uint32_t *pcur = perm, *pnext = w.perm2;
+    for (int t = 0; t < nsteps; ++t) {
+        uint32_t *start = saves ? saves->start + (size_t)t * saves->start_stride : w.start;
+        float4 *sorted = saves ? saves->sorted + (size_t)t * n : w.sorted;
+        mark(1 + 5 * t);
+        launch_key(state, sa, w, w.geo, saves ? saves->geo + (size_t)t * sa.nsims : nullptr,
+                   status, s);
+        mark(2 + 5 * t);
+        launch_scan(w, start, max_boxes, status, s);
+        mark(3 + 5 * t);
+        launch_place(w, start, n, status, s);
+        mark(4 + 5 * t);
+        launch_canon(w, start, state, pcur, sorted, pnext,
+                     saves ? saves->sigma + (size_t)t * n : nullptr, n, status, s);
+        mark(5 + 5 * t);
+        SweepOut o{};
+        o.state_out = state;
+        o.force = saves ? saves->force + (size_t)t * n : nullptr;
+        o.bounds = w.bounds;
+        o.geo_next = w.geo;
+        o.ctrl = w.ctrl;
+        o.max_boxes = max_boxes;
+        launch_sweep(kSweepStep, sorted, start, w.geo, sa, o, sweep_block, status, s);
+        std::swap(pcur, pnext);
+    }
+    mark(1 + 5 * nsteps);
+    if (pcur != perm && perm != nullptr)
+        if (cudaMemcpyAsync(perm, pcur, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s) !=
+            cudaSuccess)
+            return UG_ECUDA;
+    return last_launch();
+}
+
+// ------------------------------------------------------------------ helpers kernels
+__global__ void k_iota(uint32_t *p, uint32_t n) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = i;
+}
+__global__ void k_scatter_rows(const float4 *__restrict__ rows, const uint32_t *__restrict__ perm,
+                               uint32_t n, float4 *__restrict__ out) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[__ldg(perm + i)] = __ldg(rows + i);
+}
+__global__ void k_gather_rows(const float4 *__restrict__ rows, const uint32_t *__restrict__ perm,
+                              uint32_t n, float4 *__restrict__ out) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = __ldg(rows + __ldg(perm + i));
+}
+
+}  // namespace ug
+
+using namespace ug;
+
+static inline bool aligned(const void *p, size_t a) {
+    return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0;
+}
+static inline bool rows_ok(const void *p) { return p != nullptr && aligned(p, 16); }
+
+extern "C" {
+
+const char *ug_strerror(int status) {
+    switch (status) {
+    case UG_OK: return "ok";
+    case UG_EINVAL: return "invalid argument";
+    case UG_EBADSTATE: return "non-finite coordinate or diameter not finite and positive";
+    case UG_EGRID_TOO_LARGE: return "grid needs more boxes than max_boxes";
+    case UG_ECAPACITY: return "per-agent output list too short";
+    case UG_EWORKSPACE: return "workspace too small";
+    case UG_ETIMEOUT: return "bounded device wait timed out";
+    case UG_ECUDA: return "CUDA runtime error";
+    default: return "unknown status";
+    }
+}
+
+int ug_version(void) { return 10000; }
+
+size_t ug_workspace_bytes(uint32_t n, uint32_t nsims, uint32_t max_boxes) {
+    Workspace w;
+    return layout_workspace(nullptr, n, nsims == 0 ? 1 : nsims, max_boxes, &w);
+}
+
+int ug_grid_build(const float *state_in, const uint32_t *perm_in, uint32_t n, float contact_margin,
+                  float *state_sorted, uint32_t *perm_sorted, uint32_t *box_start,
+                  uint32_t max_boxes, ug_grid_info *info, void *ws, size_t ws_bytes,
+                  int32_t *status, void *stream) {
+    if (n == 0) return UG_OK;
+    if (!rows_ok(state_in) || !rows_ok(state_sorted) || !perm_sorted || !box_start || !info ||
+        !status || !ws || !aligned(ws, 256) || !aligned(box_start, 16) || max_boxes < 27 ||
+        !(contact_margin >= 0.0f))
+        return UG_EINVAL;
+    Workspace w;
+    if (layout_workspace(ws, n, 1, max_boxes, &w) > ws_bytes) return UG_EWORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    SimArgs sa{};
+    sa.nsims = 1;
+    sa.n = n;
+    sa.pval.contact_margin = contact_margin;
+    sa.bounds_copies = bounds_copies(1);
+    if (cudaMemsetAsync(w.ctrl, 0, zero_bytes(w), s) != cudaSuccess) return UG_ECUDA;
+    const float4 *in = reinterpret_cast<const float4 *>(state_in);
+    launch_bounds(in, sa, w, info, max_boxes, status, s);
+    launch_key(in, sa, w, info, nullptr, status, s);
+    launch_scan(w, box_start, max_boxes, status, s);
+    launch_place(w, box_start, n, status, s);
+    launch_canon(w, box_start, in, perm_in, reinterpret_cast<float4 *>(state_sorted), perm_sorted,
+                 nullptr, n, status, s);
+    return last_launch();
+}
+
+int ug_compute_forces(const float *state_sorted, const uint32_t *box_start, const ug_grid_info *info,
+                      uint32_t n, ug_params p, float *force, int32_t *status, void *stream) {
+    if (n == 0) return UG_OK;
+    if (!rows_ok(state_sorted) || !box_start || !info || !rows_ok(force) || !status) return UG_EINVAL;
+    SimArgs sa{};
+    sa.nsims = 1;
+    sa.n = n;
+    sa.pval = p;
+    sa.bounds_copies = 1;
+    SweepOut o{};
+    o.force = reinterpret_cast<float4 *>(force);
+    launch_sweep(kSweepForce, reinterpret_cast<const float4 *>(state_sorted), box_start, info, sa, o,
+                 128, status, static_cast<cudaStream_t>(stream));
+    return last_launch();
+}
+
+int ug_list_pairs(const float *state_sorted, const uint32_t *box_start, const ug_grid_info *info,
+                  uint32_t n, float contact_margin, uint32_t max_per_agent, uint32_t *count,
+                  uint32_t *nbr, int32_t *status, void *stream) {
+    if (n == 0) return UG_OK;
+    if (!rows_ok(state_sorted) || !box_start || !info || !count || (!nbr && max_per_agent) ||
+        !status)
+        return UG_EINVAL;
+    SimArgs sa{};
+    sa.nsims = 1;
+    sa.n = n;
+    sa.pval.contact_margin = contact_margin;
+    sa.bounds_copies = 1;
+    SweepOut o{};
+    o.pair_count = count;
+    o.nbr = nbr;
+    o.max_per_agent = max_per_agent;
+    launch_sweep(kSweepPairs, reinterpret_cast<const float4 *>(state_sorted), box_start, info, sa, o,
+                 128, status, static_cast<cudaStream_t>(stream));
+    return last_launch();
+}
+
+int ug_apply_displacement(const float *state_in, const float *force, uint32_t n, ug_params p,
+                          float *state_out, float *disp_out, int32_t *status, void *stream) {
+    if (n == 0) return UG_OK;
+    if (!rows_ok(state_in) || !rows_ok(force) || !rows_ok(state_out) ||
+        (disp_out && !aligned(disp_out, 16)) || !status)
+        return UG_EINVAL;
+    launch_apply(reinterpret_cast<const float4 *>(state_in), reinterpret_cast<const float4 *>(force),
+                 n, p, reinterpret_cast<float4 *>(state_out), reinterpret_cast<float4 *>(disp_out),
+                 status, static_cast<cudaStream_t>(stream));
+    return last_launch();
+}
+
+int ug_step(float *state, uint32_t *perm, uint32_t n, ug_params p, int32_t nsteps,
+            uint32_t max_boxes, void *ws, size_t ws_bytes, int32_t *status, void *stream) {
+    if (nsteps < 0) return UG_EINVAL;
+    if (n == 0 || nsteps == 0) return UG_OK;
+    if (!rows_ok(state) || !perm || !status || !ws || !aligned(ws, 256) || max_boxes < 27 ||
+        !(p.contact_margin >= 0.0f))
+        return UG_EINVAL;
+    Workspace w;
+    if (layout_workspace(ws, n, 1, max_boxes, &w) > ws_bytes) return UG_EWORKSPACE;
+    SimArgs sa{};
+    sa.nsims = 1;
+    sa.n = n;
+    sa.pval = p;
+    sa.bounds_copies = bounds_copies(1);
+    return run_steps(reinterpret_cast<float4 *>(state), perm, sa, nsteps, max_boxes, w, 128, nullptr,
+                     status, static_cast<cudaStream_t>(stream));
+}
+
+int ug_step_traced(float *state, uint32_t *perm, uint32_t n, ug_params p, int32_t nsteps,
+                   uint32_t max_boxes, void *ws, size_t ws_bytes, int32_t *status, void *stream,
+                   void *const *events, int32_t nevents) {
+    if (nsteps < 0 || !events || nevents < 2 + 5 * nsteps) return UG_EINVAL;
+    if (n == 0 || nsteps == 0) return UG_OK;
+    if (!rows_ok(state) || !perm || !status || !ws || !aligned(ws, 256) || max_boxes < 27 ||
+        !(p.contact_margin >= 0.0f))
+        return UG_EINVAL;
+    Workspace w;
+    if (layout_workspace(ws, n, 1, max_boxes, &w) > ws_bytes) return UG_EWORKSPACE;
+    SimArgs sa{};
+    sa.nsims = 1;
+    sa.n = n;
+    sa.pval = p;
+    sa.bounds_copies = bounds_copies(1);
+    return run_steps(reinterpret_cast<float4 *>(state), perm, sa, nsteps, max_boxes, w, 128, nullptr,
+                     status, static_cast<cudaStream_t>(stream),
+                     reinterpret_cast<cudaEvent_t const *>(events));
+}
+
+int ug_step_batched(float *state, uint32_t *perm, const uint32_t *sim_offset, uint32_t nsims,
+                    uint32_t n_total, const ug_params *params, int32_t nsteps, uint32_t max_boxes,
+                    const ug_tuning *tuning, void *ws, size_t ws_bytes, int32_t *status,
+                    void *stream) {
+    if (nsteps < 0) return UG_EINVAL;
+    if (n_total == 0 || nsteps == 0) return UG_OK;
+    if (!rows_ok(state) || !perm || !sim_offset || nsims == 0 || !params || !status || !ws ||
+        !aligned(ws, 256) || max_boxes < 27)
+        return UG_EINVAL;
+    Workspace w;
+    if (layout_workspace(ws, n_total, nsims, max_boxes, &w) > ws_bytes) return UG_EWORKSPACE;
+    SimArgs sa{};
+    sa.offset = sim_offset;
+    sa.pdev = params;
+    sa.nsims = nsims;
+    sa.n = n_total;
+    sa.bounds_copies = bounds_copies(nsims);
+    int block = tuning && tuning->sweep_block ? tuning->sweep_block : 128;
+    if (block != 64 && block != 128 && block != 256) return UG_EINVAL;
+    return run_steps(reinterpret_cast<float4 *>(state), perm, sa, nsteps, max_boxes, w, block,
+                     nullptr, status, static_cast<cudaStream_t>(stream));
+}
+
+int ug_tune_batched(const float *state, const uint32_t *sim_offset, uint32_t nsims, uint32_t n_total,
+                    const ug_params *params, uint32_t max_boxes, ug_tuning *best, void *ws,
+                    size_t ws_bytes, void *stream) {
+    if (!best) return UG_EINVAL;
+    memset(best, 0, sizeof(*best));
+    best->sweep_block = 128;
+    if (n_total == 0) return UG_OK;
+    if (!rows_ok(state) || !sim_offset || nsims == 0 || !params || !ws || !aligned(ws, 256) ||
+        max_boxes < 27)
+        return UG_EINVAL;
+    Workspace w;
+    const size_t base = layout_workspace(ws, n_total, nsims, max_boxes, &w);
+    const size_t need = base + align256(sizeof(float4) * (size_t)n_total) + 256;
+    if (need > ws_bytes) return UG_EWORKSPACE;
+    float4 *force = reinterpret_cast<float4 *>(static_cast<char *>(ws) + base);
+    int32_t *status = reinterpret_cast<int32_t *>(static_cast<char *>(ws) + base +
+                                                  align256(sizeof(float4) * (size_t)n_total));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    SimArgs sa{};
+    sa.offset = sim_offset;
+    sa.pdev = params;
+    sa.nsims = nsims;
+    sa.n = n_total;
+    sa.bounds_copies = bounds_copies(nsims);
+    if (cudaMemsetAsync(w.ctrl, 0, zero_bytes(w), s) != cudaSuccess) return UG_ECUDA;
+    if (cudaMemsetAsync(status, 0, sizeof(int32_t), s) != cudaSuccess) return UG_ECUDA;
+    const float4 *in = reinterpret_cast<const float4 *>(state);
+    launch_bounds(in, sa, w, w.geo, max_boxes, status, s);
+    launch_key(in, sa, w, w.geo, nullptr, status, s);
+    launch_scan(w, w.start, max_boxes, status, s);
+    launch_place(w, w.start, n_total, status, s);
+    launch_canon(w, w.start, in, nullptr, w.sorted, w.perm2, nullptr, n_total, status, s);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return UG_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return UG_ECUDA; }
+    const int cands[3] = {64, 128, 256};
+    float best_ms = 1e30f;
+    int rc = UG_OK;
+    for (int c = 0; c < 3 && rc == UG_OK; ++c) {
+        SweepOut o{};
+        o.force = force;
+        launch_sweep(kSweepForce, w.sorted, w.start, w.geo, sa, o, cands[c], status, s);   // warm
+        cudaEventRecord(e0, s);
+        for (int rep = 0; rep < 3; ++rep)
+            launch_sweep(kSweepForce, w.sorted, w.start, w.geo, sa, o, cands[c], status, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = UG_ECUDA; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) { best_ms = ms; best->sweep_block = cands[c]; }
+    }
+    int32_t hst = 0;
+    if (rc == UG_OK && cudaMemcpy(&hst, status, sizeof(hst), cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = UG_ECUDA;
+    if (rc == UG_OK && hst != 0) rc = hst;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == UG_OK) rc = last_launch();
+    return rc;
+}
+
+int ug_iota(uint32_t *perm, uint32_t n, void *stream) {
+    if (n == 0) return UG_OK;
+    if (!perm) return UG_EINVAL;
+    k_iota<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(perm, n);
+    return last_launch();
+}
+
+int ug_scatter_rows(const float *rows, const uint32_t *perm, uint32_t n, float *rows_by_id,
+                    void *stream) {
+    if (n == 0) return UG_OK;
+    if (!rows_ok(rows) || !perm || !rows_ok(rows_by_id)) return UG_EINVAL;
+    k_scatter_rows<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const float4 *>(rows), perm, n, reinterpret_cast<float4 *>(rows_by_id));
+    return last_launch();
+}
+
+int ug_gather_rows(const float *rows_by_id, const uint32_t *perm, uint32_t n, float *rows,
+                   void *stream) {
+    if (n == 0) return UG_OK;
+    if (!rows_ok(rows_by_id) || !perm || !rows_ok(rows)) return UG_EINVAL;
+    k_gather_rows<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const float4 *>(rows_by_id), perm, n, reinterpret_cast<float4 *>(rows));
+    return last_launch();
+}
+
+}  // extern "C"

@@ -1,0 +1,249 @@
+// Uniform-grid construction (Hesam et al., Sec. IV-A and IV-D), GB300 design.
+//
+// The paper keeps a per-box count plus a linked list of agents and sorts agent
+// state along a Z-order curve so that neighbours share cache lines.  Here the
+// grid IS the sort: a counting sort by box key, boxes in row-major order (x
+// fastest, so the three boxes of a neighbourhood along x are one contiguous
+// run), agents of a box in their input order.  Five kernels per rebuild:
+//
+//   k_bounds  (first step only; later steps get it from the sweep epilogue)
+//             per-simulation min/max corner and max diameter -> grid geometry
+//   k_key     box key of every row + warp-aggregated atomic histogram; the
+//             atomic's return value is a provisional rank inside the box
+//   k_scan    single-pass exclusive scan of the box counts with decoupled
+//             look-back (bounded spins), also re-zeroing the counts
+//   k_place   row index -> provisional slot
+//   k_canon   stable order inside each box (rank = rows of the box with a
+//             smaller input index), gathering rows and ids into that slot
+#include <cuda_runtime.h>
+
+#include "ug_internal.cuh"
+
+namespace ug {
+
+// ------------------------------------------------------------------ bounds
+__global__ void __launch_bounds__(256)
+k_bounds(const float4 *__restrict__ st, SimArgs sa, uint32_t *bounds, ug_grid_info *geo,
+         Ctrl *ctrl, uint32_t max_boxes, int32_t *status) {
+    if (cta_failed(status)) return;
+    const uint32_t first = blockIdx.x * blockDim.x;
+    const uint32_t i = first + threadIdx.x;
+    const bool valid = i < sa.n;
+    bool uniform;
+    const uint32_t sim = cta_sim(sa, first, i, uniform);
+    const float4 p = valid ? __ldg(st + i) : make_float4(0.f, 0.f, 0.f, 1.f);
+    accumulate_bounds(sa, p, valid, sim, uniform, bounds, status);
+    if (elect_last_cta(&ctrl->done)) finalize_grid(sa, bounds, geo, ctrl, max_boxes, status);
+}
+
+// ------------------------------------------------------------------ key + histogram
+__global__ void __launch_bounds__(256)
+k_key(const float4 *__restrict__ st, SimArgs sa, const ug_grid_info *__restrict__ geo,
+      Ctrl *ctrl, uint32_t *counts, uint32_t *__restrict__ key, uint32_t *__restrict__ rank,
+      unsigned long long *scan_status, uint32_t ntiles, ug_grid_info *geo_save,
+      int32_t *status) {
+    const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t t = gtid; t < ntiles; t += stride) scan_status[t] = 0ull;
+    if (gtid == 0) ctrl->scan_ticket = 0u;
+    if (geo_save)
+        for (uint32_t s = gtid; s < sa.nsims; s += stride) geo_save[s] = geo[s];
+    if (cta_failed(status)) return;
+
+    const uint32_t first = blockIdx.x * blockDim.x;
+    const uint32_t i = first + threadIdx.x;
+    const bool valid = i < sa.n;
+    bool uniform;
+    const uint32_t sim = cta_sim(sa, first, i, uniform);
+    const unsigned act = __ballot_sync(kFull, valid);
+    if (!valid) return;
+    const ug_grid_info g = geo[sim];
+    int bx, by, bz;
+    const uint32_t k = box_key(__ldg(st + i), g, bx, by, bz);
+    // rows of this warp with the same key share one atomic
+    const unsigned peers = __match_any_sync(act, k);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&counts[k], (uint32_t)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    rank[i] = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+    key[i] = k;
+}
+
+// ------------------------------------------------------------------ look-back scan
+// Tile status word: flag << 32 | value; flag 0 = not ready, 1 = tile sum only,
+// 2 = inclusive prefix of everything up to and including the tile.
+__device__ __forceinline__ void publish(unsigned long long *st, uint32_t t, uint32_t flag,
+                                        uint32_t val) {
+    *(volatile unsigned long long *)(st + t) = ((unsigned long long)flag << 32) | val;
+}
+
+__device__ uint32_t look_back(unsigned long long *st, uint32_t t, int32_t *status) {
+    uint32_t excl = 0;
+    int j = (int)t - 1;
+    uint32_t spins = 0;
+    while (j >= 0) {
+        const unsigned long long w = *(volatile unsigned long long *)(st + j);
+        const uint32_t flag = (uint32_t)(w >> 32);
+        if (flag == 0u) {
+            if (++spins > kSpinLimit || peek_status(status) != 0) {
+                set_status(status, UG_ETIMEOUT);
+                return excl;
+            }
+            __nanosleep(64);
+            continue;
+        }
+        excl += (uint32_t)w;
+        if (flag == 2u) break;
+        --j;
+    }
+    return excl;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan(uint32_t *__restrict__ counts, uint32_t *__restrict__ start, Ctrl *ctrl,
+       unsigned long long *tstat, int32_t *status) {
+    __shared__ uint32_t s_tile, s_prefix;
+    __shared__ uint32_t s_warp[kScanThreads / 32];
+    if (cta_failed(status)) return;
+    const uint32_t B = *(volatile uint32_t *)&ctrl->total_boxes;
+    const uint32_t ntiles = (B + kScanTile - 1) / kScanTile;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(&ctrl->scan_ticket, 1u);
+        __syncthreads();
+        const uint32_t t = s_tile;
+        if (t >= ntiles) break;
+        const uint32_t base = t * kScanTile + threadIdx.x * kScanItems;
+        uint32_t v[kScanItems];
+        if (base + kScanItems <= B) {
+            const uint4 a = *reinterpret_cast<const uint4 *>(counts + base);
+            const uint4 b = *reinterpret_cast<const uint4 *>(counts + base + 4);
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < kScanItems; ++k) v[k] = base + k < B ? counts[base + k] : 0u;
+        }
+        uint32_t tsum = 0;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) tsum += v[k];
+        // warp inclusive scan of thread sums
+        uint32_t inc = tsum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) s_warp[warp] = inc;
+        __syncthreads();
+        uint32_t wbase = 0, tile_total = 0;
+#pragma unroll
+        for (int w = 0; w < kScanThreads / 32; ++w) {
+            const uint32_t x = s_warp[w];
+            if (w < warp) wbase += x;
+            tile_total += x;
+        }
+        if (threadIdx.x == 0) {
+            uint32_t excl = 0;
+            if (t == 0) {
+                publish(tstat, t, 2u, tile_total);
+            } else {
+                publish(tstat, t, 1u, tile_total);
+                excl = look_back(tstat, t, status);
+                publish(tstat, t, 2u, excl + tile_total);
+            }
+            s_prefix = excl;
+        }
+        __syncthreads();
+        uint32_t run = s_prefix + wbase + inc - tsum;
+        if (base + kScanItems <= B) {
+            uint4 a, b;
+            a.x = run; run += v[0]; a.y = run; run += v[1]; a.z = run; run += v[2]; a.w = run; run += v[3];
+            b.x = run; run += v[4]; b.y = run; run += v[5]; b.z = run; run += v[6]; b.w = run; run += v[7];
+            *reinterpret_cast<uint4 *>(start + base) = a;
+            *reinterpret_cast<uint4 *>(start + base + 4) = b;
+            *reinterpret_cast<uint4 *>(counts + base) = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4 *>(counts + base + 4) = make_uint4(0u, 0u, 0u, 0u);
+        } else {
+#pragma unroll
+            for (int k = 0; k < kScanItems; ++k) {
+                if (base + k < B) {
+                    start[base + k] = run;
+                    counts[base + k] = 0u;
+                }
+                run += v[k];
+            }
+        }
+        if (t == ntiles - 1 && threadIdx.x == 0) start[B] = s_prefix + tile_total;
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ placement
+__global__ void __launch_bounds__(256)
+k_place(const uint32_t *__restrict__ key, const uint32_t *__restrict__ rank,
+        const uint32_t *__restrict__ start, uint32_t *__restrict__ tmp, uint32_t n,
+        int32_t *status) {
+    if (cta_failed(status)) return;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) tmp[__ldg(start + __ldg(key + i)) + __ldg(rank + i)] = i;
+}
+
+__global__ void __launch_bounds__(256)
+k_canon(const uint32_t *__restrict__ tmp, const uint32_t *__restrict__ key,
+        const uint32_t *__restrict__ start, const float4 *__restrict__ st_in,
+        const uint32_t *__restrict__ perm_in, float4 *__restrict__ st_out,
+        uint32_t *__restrict__ perm_out, uint32_t *__restrict__ sigma, uint32_t n,
+        int32_t *status) {
+    if (cta_failed(status)) return;
+    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const uint32_t id = __ldg(tmp + s);
+    const uint32_t k = __ldg(key + id);
+    const uint32_t b0 = __ldg(start + k), b1 = __ldg(start + k + 1);
+    uint32_t r = 0;
+    for (uint32_t t = b0; t < b1; ++t) r += __ldg(tmp + t) < id;
+    const uint32_t dest = b0 + r;
+    st_out[dest] = __ldg(st_in + id);
+    perm_out[dest] = perm_in ? __ldg(perm_in + id) : id;
+    if (sigma) sigma[dest] = id;
+}
+
+// ------------------------------------------------------------------ launchers
+static inline unsigned blocks_for(uint32_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+void launch_bounds(const float4 *st, const SimArgs &sa, const Workspace &w, ug_grid_info *geo,
+                   uint32_t max_boxes, int32_t *status, cudaStream_t s) {
+    k_bounds<<<blocks_for(sa.n, 256), 256, 0, s>>>(st, sa, w.bounds, geo, w.ctrl, max_boxes,
+                                                   status);
+}
+
+void launch_key(const float4 *st, const SimArgs &sa, const Workspace &w, const ug_grid_info *geo,
+                ug_grid_info *geo_save, int32_t *status, cudaStream_t s) {
+    k_key<<<blocks_for(sa.n, 256), 256, 0, s>>>(st, sa, geo, w.ctrl, w.counts, w.key, w.rank,
+                                                w.scan_status, w.ntiles, geo_save, status);
+}
+
+void launch_scan(const Workspace &w, uint32_t *start, uint32_t max_boxes, int32_t *status,
+                 cudaStream_t s) {
+    (void)max_boxes;
+    const unsigned grid = (unsigned)min((int)w.ntiles, 4 * device_sm_count());
+    k_scan<<<grid > 0 ? grid : 1, kScanThreads, 0, s>>>(w.counts, start, w.ctrl, w.scan_status,
+                                                         status);
+}
+
+void launch_place(const Workspace &w, const uint32_t *start, uint32_t n, int32_t *status,
+                  cudaStream_t s) {
+    k_place<<<blocks_for(n, 256), 256, 0, s>>>(w.key, w.rank, start, w.tmp, n, status);
+}
+
+void launch_canon(const Workspace &w, const uint32_t *start, const float4 *st_in,
+                  const uint32_t *perm_in, float4 *st_sorted, uint32_t *perm_out, uint32_t *sigma,
+                  uint32_t n, int32_t *status, cudaStream_t s) {
+    k_canon<<<blocks_for(n, 256), 256, 0, s>>>(w.tmp, w.key, start, st_in, perm_in, st_sorted,
+                                               perm_out, sigma, n, status);
+}
+
+}  // namespace ug

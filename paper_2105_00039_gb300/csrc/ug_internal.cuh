@@ -1,0 +1,491 @@
+// Internal declarations shared by the library's translation units.
+// Device helpers are header-inline; host launchers are defined in the .cu files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "ugmech.h"
+
+namespace ug {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;   // boxes per look-back tile
+constexpr int kBoundsWords = 8;                         // per simulation, see bounds_*()
+constexpr int kBoundsCopiesSingle = 32;                 // spread atomics when nsims == 1
+constexpr uint32_t kSpinLimit = 1u << 22;               // bounded waits (x ~64 ns sleep)
+
+// Control words living in the workspace (zeroed at the start of every call).
+struct Ctrl {
+    uint32_t scan_ticket;   // dynamic tile index of the look-back scan
+    uint32_t done;          // CTAs finished (last-CTA pattern of the bounds reduction)
+    uint32_t total_boxes;   // boxes of the current grid (all sims); 0 after an error
+    uint32_t adj_done;      // last-CTA counter of the adjoint parameter reduction
+    uint32_t pad[4];
+};
+
+// Which simulation owns which rows, and its constants.
+struct SimArgs {
+    const uint32_t *offset;   // [nsims + 1] device, or nullptr: one simulation over [0, n)
+    const ug_params *pdev;    // [nsims] device, or nullptr: pval for all
+    ug_params pval;
+    uint32_t nsims;
+    uint32_t n;
+    uint32_t bounds_copies;   // copies of the bounds accumulators (atomic spreading)
+};
+
+// ------------------------------------------------------------------ status
+__device__ __forceinline__ void set_status(int32_t *status, int32_t code) {
+    atomicCAS(status, 0, code);
+}
+__device__ __forceinline__ int32_t peek_status(const int32_t *status) {
+    return *(volatile const int32_t *)status;
+}
+// Block-uniform early exit: every thread of the CTA must call it.
+__device__ __forceinline__ bool cta_failed(const int32_t *status) {
+    __shared__ int s_fail;
+    if (threadIdx.x == 0) s_fail = peek_status(status) != 0;
+    __syncthreads();
+    return s_fail != 0;
+}
+
+// ------------------------------------------------------------------ simulations
+__device__ __forceinline__ uint32_t find_sim(const SimArgs &sa, uint32_t i) {
+    if (sa.offset == nullptr || sa.nsims <= 1) return 0;
+    uint32_t lo = 0, hi = sa.nsims;   // offset[lo] <= i < offset[hi]
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(sa.offset + mid) <= i) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+__device__ __forceinline__ uint32_t sim_begin(const SimArgs &sa, uint32_t s) {
+    return sa.offset ? __ldg(sa.offset + s) : 0u;
+}
+__device__ __forceinline__ uint32_t sim_end(const SimArgs &sa, uint32_t s) {
+    return sa.offset ? __ldg(sa.offset + s + 1) : sa.n;
+}
+__device__ __forceinline__ ug_params sim_params(const SimArgs &sa, uint32_t s) {
+    return sa.pdev ? sa.pdev[s] : sa.pval;
+}
+// Simulation of row i, resolved once per CTA when the CTA's rows share one.
+// Every thread must call it.  `uniform` tells whether they do.
+__device__ __forceinline__ uint32_t cta_sim(const SimArgs &sa, uint32_t first, uint32_t i,
+                                            bool &uniform) {
+    __shared__ uint32_t s_sim[2];
+    if (sa.offset == nullptr || sa.nsims <= 1) { uniform = true; return 0; }
+    if (threadIdx.x == 0) {
+        const uint32_t last = min(first + blockDim.x, sa.n) - 1;
+        s_sim[0] = find_sim(sa, min(first, sa.n - 1));
+        s_sim[1] = find_sim(sa, last);
+    }
+    __syncthreads();
+    uniform = s_sim[0] == s_sim[1];
+    return uniform ? s_sim[0] : find_sim(sa, min(i, sa.n - 1));
+}
+
+// ------------------------------------------------------------------ ordered floats
+// Monotone map float -> uint32 (larger float, larger code); 0 is below every
+// float, so a zeroed word is the identity of atomicMax.
+__device__ __forceinline__ uint32_t ord_enc(float f) {
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord_dec(uint32_t e) {
+    return __uint_as_float((e & 0x80000000u) ? (e & 0x7fffffffu) : ~e);
+}
+
+// ------------------------------------------------------------------ grid geometry
+// Box coordinate along one axis: max(floor((p - o) / e), 1), IEEE round-to-nearest
+// subtraction and division (the oracle evaluates the same expression in float32).
+// The upper clamp never binds for rows the geometry was built from.
+__device__ __forceinline__ int box_coord(float p, float o, float e, int dim) {
+    const float f = floorf(__fdiv_rn(__fsub_rn(p, o), e));
+    int b = (int)f;
+    b = max(b, 1);
+    b = min(b, dim - 2);
+    return b;
+}
+__device__ __forceinline__ uint32_t box_key(const float4 &p, const ug_grid_info &g,
+                                            int &bx, int &by, int &bz) {
+    bx = box_coord(p.x, g.origin[0], g.edge, g.dims[0]);
+    by = box_coord(p.y, g.origin[1], g.edge, g.dims[1]);
+    bz = box_coord(p.z, g.origin[2], g.edge, g.dims[2]);
+    return g.box_base + (uint32_t)((bz * g.dims[1] + by) * g.dims[0] + bx);
+}
+
+// ------------------------------------------------------------------ float-float
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    const float ap = __fsub_rn(s, bp);
+    e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+// Compensated accumulation (Knuth TwoSum, Neumaier-style running error).
+__device__ __forceinline__ void comp_add(float &s, float &c, float x) {
+    float t, e;
+    two_sum(s, x, t, e);
+    s = t;
+    c = __fadd_rn(c, e);
+}
+
+// Contact test of Eq. 1 in float-float arithmetic.
+//   a, b: rows (x, y, z, d); ra = a.w / 2; m2 = 2 * contact margin.
+// q = s^2 - d^2 with s = ra + rb + m2 is formed from exact differences, exact
+// squares and TwoSums, so its sign (the predicate delta > 0) and value are exact
+// to ~1e-12 of s^2; delta = q / (s + d) then carries ~3 ulp of relative error.
+// Returns false for no contact or coincident centres (d = 0).
+struct ContactGeo {
+    float delta;   // overlap
+    float invd;    // 1 / |p_a - p_b|
+    float hx, hy, hz;   // p_a - p_b (rounded)
+    float rb;      // radius of b
+    float rsum;    // ra + rb (rounded)
+};
+__device__ __forceinline__ bool contact(const float4 &a, float ra, const float4 &b, float m2,
+                                        ContactGeo &c) {
+    float lx, ly, lz;
+    two_sum(a.x, -b.x, c.hx, lx);
+    two_sum(a.y, -b.y, c.hy, ly);
+    two_sum(a.z, -b.z, c.hz, lz);
+    float px, ex, py, ey, pz, ez;
+    two_prod(c.hx, c.hx, px, ex);
+    two_prod(c.hy, c.hy, py, ey);
+    two_prod(c.hz, c.hz, pz, ez);
+    float s1, e1, D, e2;
+    two_sum(px, py, s1, e1);
+    two_sum(s1, pz, D, e2);
+    const float E = ex + ey + ez + e1 + e2 + 2.0f * (c.hx * lx + c.hy * ly + c.hz * lz);
+    c.rb = 0.5f * b.w;
+    float sh, sl;
+    two_sum(ra, c.rb, sh, sl);
+    c.rsum = sh;
+    if (m2 != 0.0f) {
+        float t, te;
+        two_sum(sh, m2, t, te);
+        sh = t;
+        sl = sl + te;
+    }
+    float S2, S2e;
+    two_prod(sh, sh, S2, S2e);
+    S2e = fmaf(2.0f * sh, sl, S2e);
+    const float q = __fsub_rn(S2, D) + (S2e - E);
+    if (!(q > 0.0f) || !(D > 0.0f)) return false;
+    c.invd = rsqrtf(D);
+    const float d = D * c.invd;
+    c.delta = __fdividef(q, sh + d);
+    return true;
+}
+
+// ------------------------------------------------------------------ neighbour traversal
+// With boxes numbered x-fastest the 27 boxes around (bx, by, bz) are 9 runs of 3
+// consecutive boxes, one per (dy, dz); run r covers sorted slots
+// start[key(bx-1, by+dy, bz+dz)] .. start[key(bx+1, by+dy, bz+dz) + 1].
+constexpr int kListCap = 16;
+constexpr float kFilter = 1.0f + 1.0f / 65536.0f;
+
+__device__ __forceinline__ uint32_t run_row_key(const ug_grid_info &g, int bx, int by, int bz,
+                                                int r) {
+    const int dy = r % 3 - 1, dz = r / 3 - 1;
+    return g.box_base + (uint32_t)(((bz + dz) * g.dims[1] + (by + dy)) * g.dims[0] + bx);
+}
+
+// Visit every candidate j != i of the 27 boxes around row i; `fn(j, row_j)` is
+// called for those passing a float32 distance filter whose 2^-16 relative band
+// keeps every true contact (the exact test is fn's job).  Candidates are
+// buffered per lane in `lst` and handed to fn in warp-converged batches.  All
+// 32 lanes of every warp must call this (invalid lanes pass valid = false).
+template <int T, typename Fn>
+__device__ __forceinline__ void sweep_neighbours(const float4 *__restrict__ st,
+                                                 const uint32_t *__restrict__ start,
+                                                 const ug_grid_info &g, uint32_t i, bool valid,
+                                                 const float4 &me, float m2,
+                                                 uint32_t (*lst)[T], Fn &&fn) {
+    int bx = 1, by = 1, bz = 1;
+    int total = 0;
+    if (valid) {
+        box_key(me, g, bx, by, bz);
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
+            const uint32_t kb = run_row_key(g, bx, by, bz, r);
+            total += (int)(__ldg(start + kb + 2) - __ldg(start + kb - 1));
+        }
+    }
+    const float rim = 0.5f * me.w + m2;
+    const int tmax = (int)__reduce_max_sync(kFull, (unsigned)total);
+    int cnt = 0;
+    int r = -1;
+    uint32_t j = 0, jend = 0;
+    auto flush = [&]() {
+        const int m = (int)__reduce_max_sync(kFull, (unsigned)cnt);
+        for (int k = 0; k < m; ++k) {
+            if (k < cnt) {
+                const uint32_t jj = lst[k][threadIdx.x];
+                fn(jj, __ldg(st + jj));
+            }
+        }
+        cnt = 0;
+    };
+    for (int t = 0; t < tmax; ++t) {
+        if (t < total) {
+            while (j >= jend) {
+                ++r;
+                const uint32_t kb = run_row_key(g, bx, by, bz, r);
+                j = __ldg(start + kb - 1);
+                jend = __ldg(start + kb + 2);
+            }
+            const float4 q = __ldg(st + j);
+            const float dx = me.x - q.x, dy = me.y - q.y, dz = me.z - q.z;
+            const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const float s = fmaf(0.5f, q.w, rim);
+            if (d2 < s * s * kFilter && j != i) {
+                lst[cnt][threadIdx.x] = j;
+                ++cnt;
+            }
+            ++j;
+        }
+        if (__any_sync(kFull, cnt == kListCap)) flush();
+    }
+    flush();
+}
+
+// ------------------------------------------------------------------ displacement
+// Sec. III readings: moving iff |F| > adherence; v = dt/m F, m = rho pi/6 d^3;
+// |v| capped at max_disp.  Returns u; *moving and *vn for the adjoint.
+__device__ __forceinline__ float3 displacement(float Fx, float Fy, float Fz, float diam,
+                                               const ug_params &P, bool *moving_out = nullptr,
+                                               bool *capped_out = nullptr) {
+    const float Fn = sqrtf(Fx * Fx + Fy * Fy + Fz * Fz);
+    float3 u = make_float3(0.f, 0.f, 0.f);
+    bool moving = Fn > P.adherence, capped = false;
+    if (moving) {
+        const float m = P.density * (float)(M_PI / 6.0) * diam * diam * diam;
+        const float c = P.dt / m;
+        u = make_float3(c * Fx, c * Fy, c * Fz);
+        const float vn = sqrtf(u.x * u.x + u.y * u.y + u.z * u.z);
+        if (vn > P.max_disp) {
+            const float s = P.max_disp / vn;
+            u = make_float3(u.x * s, u.y * s, u.z * s);
+            capped = true;
+        }
+    }
+    if (moving_out) *moving_out = moving;
+    if (capped_out) *capped_out = capped;
+    return u;
+}
+
+// ------------------------------------------------------------------ bounds
+// Per simulation and copy, kBoundsWords ordered codes maximised with atomicMax:
+//   0..2 -min(x,y,z)   3..5 max(x,y,z)   6 max diameter   7 -min diameter
+__device__ __forceinline__ void bounds_codes(const float4 &p, bool valid, uint32_t v[8]) {
+    v[0] = valid ? ord_enc(-p.x) : 0u;
+    v[1] = valid ? ord_enc(-p.y) : 0u;
+    v[2] = valid ? ord_enc(-p.z) : 0u;
+    v[3] = valid ? ord_enc(p.x) : 0u;
+    v[4] = valid ? ord_enc(p.y) : 0u;
+    v[5] = valid ? ord_enc(p.z) : 0u;
+    v[6] = valid ? ord_enc(p.w) : 0u;
+    v[7] = valid ? ord_enc(-p.w) : 0u;
+}
+__device__ __forceinline__ bool row_ok(const float4 &p) {
+    return isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && isfinite(p.w) && p.w > 0.0f;
+}
+
+// Accumulate the bounds of one row per thread; every thread of the CTA calls it.
+__device__ __forceinline__ void accumulate_bounds(const SimArgs &sa, const float4 &p, bool valid,
+                                                  uint32_t sim, bool uniform, uint32_t *bounds,
+                                                  int32_t *status) {
+    __shared__ uint32_t s_red[32][kBoundsWords];
+    if (valid && !row_ok(p)) set_status(status, UG_EBADSTATE);
+    uint32_t v[8];
+    bounds_codes(p, valid, v);
+    const uint32_t copy = sa.bounds_copies > 1 ? blockIdx.x % sa.bounds_copies : 0u;
+    if (uniform) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = __reduce_max_sync(kFull, v[k]);
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) s_red[warp][k] = v[k];
+        }
+        __syncthreads();
+        if (threadIdx.x < 8) {
+            uint32_t m = 0;
+            const int nw = (blockDim.x + 31) >> 5;
+            for (int w = 0; w < nw; ++w) m = max(m, s_red[w][threadIdx.x]);
+            if (m) atomicMax(&bounds[((size_t)copy * sa.nsims + sim) * kBoundsWords + threadIdx.x], m);
+        }
+    } else if (valid) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            atomicMax(&bounds[((size_t)copy * sa.nsims + sim) * kBoundsWords + k], v[k]);
+    }
+}
+
+// Run by the last CTA to finish: turn the bounds into each simulation's grid,
+// assign box ranges, check capacity, and reset the accumulators for next time.
+__device__ __forceinline__ void finalize_grid(const SimArgs &sa, uint32_t *bounds,
+                                              ug_grid_info *geo, Ctrl *ctrl, uint32_t max_boxes,
+                                              int32_t *status) {
+    __shared__ unsigned long long s_scan[256];   // blockDim.x <= 256 for every caller
+    __shared__ unsigned long long s_carry;
+    __shared__ int s_bad;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) { s_carry = 0; s_bad = 0; }
+    __syncthreads();
+    for (uint32_t c0 = 0; c0 < sa.nsims; c0 += nt) {
+        const uint32_t s = c0 + tid;
+        unsigned long long nb = 0;
+        ug_grid_info g{};
+        if (s < sa.nsims) {
+            const uint32_t a0 = sim_begin(sa, s), a1 = sim_end(sa, s);
+            g.agent_base = a0;
+            g.nagents = a1 - a0;
+            if (a1 > a0) {
+                uint32_t w[8];
+                for (int k = 0; k < 8; ++k) {
+                    uint32_t m = 0;
+                    for (uint32_t cp = 0; cp < sa.bounds_copies; ++cp) {
+                        uint32_t *slot = &bounds[((size_t)cp * sa.nsims + s) * kBoundsWords + k];
+                        m = max(m, *(volatile uint32_t *)slot);
+                        *slot = 0u;
+                    }
+                    w[k] = m;
+                }
+                const ug_params P = sim_params(sa, s);
+                const float m2 = 2.0f * P.contact_margin;
+                const float e = __fadd_rn(ord_dec(w[6]), m2);
+                const float mind = -ord_dec(w[7]);
+                bool bad = !(e > 0.0f) || !isfinite(e) || !(mind > 0.0f);
+                g.edge = e;
+                for (int a = 0; a < 3; ++a) {
+                    const float lo = -ord_dec(w[a]);
+                    const float hi = ord_dec(w[3 + a]);
+                    const float o = __fsub_rn(lo, e);
+                    const float f = floorf(__fdiv_rn(__fsub_rn(hi, o), e));
+                    g.origin[a] = o;
+                    if (!(f < 2097152.0f) || !isfinite(lo) || !isfinite(hi)) { bad = true; g.dims[a] = 3; }
+                    else g.dims[a] = max((int)f, 1) + 2;
+                }
+                if (bad) { atomicOr(&s_bad, 1); nb = 0; }
+                else nb = (unsigned long long)g.dims[0] * g.dims[1] * g.dims[2];
+            }
+        }
+        // block exclusive scan of nb (Hillis-Steele on nt <= 256 entries)
+        s_scan[tid] = nb;
+        __syncthreads();
+        for (int off = 1; off < nt; off <<= 1) {
+            const unsigned long long add = tid >= off ? s_scan[tid - off] : 0ull;
+            __syncthreads();
+            s_scan[tid] += add;
+            __syncthreads();
+        }
+        const unsigned long long incl = s_scan[tid];
+        const unsigned long long base = s_carry + incl - nb;
+        if (s < sa.nsims) {
+            g.box_base = (uint32_t)min(base, 0xffffffffull);
+            g.nboxes = (uint32_t)nb;
+            geo[s] = g;
+        }
+        __syncthreads();
+        if (tid == nt - 1) s_carry += incl;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        if (s_bad) set_status(status, UG_EBADSTATE);
+        const unsigned long long total = s_carry;
+        if (total > (unsigned long long)max_boxes) set_status(status, UG_EGRID_TOO_LARGE);
+        ctrl->total_boxes = (s_bad || total > max_boxes) ? 0u : (uint32_t)total;
+        ctrl->done = 0;
+        __threadfence();
+    }
+}
+
+// Last-CTA election after a grid-wide accumulation.  Every thread calls it.
+__device__ __forceinline__ bool elect_last_cta(uint32_t *counter) {
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t prev = atomicAdd(counter, 1u);
+        s_last = prev == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last != 0;
+}
+
+// ------------------------------------------------------------------ workspace
+struct Workspace {
+    uint32_t *counts;      // [max_boxes]     zero between steps
+    uint32_t *start;       // [max_boxes + 1]
+    uint32_t *key;         // [n]
+    uint32_t *rank;        // [n]
+    uint32_t *tmp;         // [n]
+    float4 *sorted;        // [n]
+    uint32_t *perm2;       // [n]
+    ug_grid_info *geo;     // [nsims]
+    uint32_t *bounds;      // [copies * nsims * 8]
+    unsigned long long *scan_status;   // [ntiles]
+    Ctrl *ctrl;
+    uint32_t ntiles;
+    size_t bytes;
+};
+
+size_t layout_workspace(void *base, uint32_t n, uint32_t nsims, uint32_t max_boxes, Workspace *w);
+int device_sm_count();
+
+// ------------------------------------------------------------------ launchers
+// Grid build pieces (ug_grid.cu).  All asynchronous on `s`.
+void launch_bounds(const float4 *st, const SimArgs &sa, const Workspace &w, ug_grid_info *geo,
+                   uint32_t max_boxes, int32_t *status, cudaStream_t s);
+void launch_key(const float4 *st, const SimArgs &sa, const Workspace &w, const ug_grid_info *geo,
+                ug_grid_info *geo_save, int32_t *status, cudaStream_t s);
+void launch_scan(const Workspace &w, uint32_t *start, uint32_t max_boxes, int32_t *status,
+                 cudaStream_t s);
+void launch_place(const Workspace &w, const uint32_t *start, uint32_t n, int32_t *status,
+                  cudaStream_t s);
+void launch_canon(const Workspace &w, const uint32_t *start, const float4 *st_in,
+                  const uint32_t *perm_in, float4 *st_sorted, uint32_t *perm_out, uint32_t *sigma,
+                  uint32_t n, int32_t *status, cudaStream_t s);
+
+// Sweep (ug_sweep.cu).
+enum SweepMode { kSweepForce = 0, kSweepStep = 1, kSweepPairs = 2 };
+struct SweepOut {
+    float4 *force;          // kSweepForce: required; kSweepStep: optional save of F
+    float4 *state_out;      // kSweepStep
+    uint32_t *bounds;       // kSweepStep: next bounds accumulators
+    ug_grid_info *geo_next; // kSweepStep: finalised geometry for the next step
+    Ctrl *ctrl;
+    uint32_t max_boxes;
+    uint32_t *pair_count;   // kSweepPairs
+    uint32_t *nbr;
+    uint32_t max_per_agent;
+};
+void launch_sweep(int mode, const float4 *sorted, const uint32_t *start, const ug_grid_info *geo,
+                  const SimArgs &sa, const SweepOut &out, int block, int32_t *status,
+                  cudaStream_t s);
+void launch_apply(const float4 *st_in, const float4 *force, uint32_t n, const ug_params &p,
+                  float4 *st_out, float4 *disp_out, int32_t *status, cudaStream_t s);
+
+// Full forward steps (ug_api.cu); used by ug_step, ug_step_batched and the adjoint.
+struct StepSaves {          // per-step records for the adjoint (nullable)
+    float4 *sorted;         // [nsteps][n]
+    uint32_t *sigma;        // [nsteps][n] sorted slot -> input row
+    uint32_t *start;        // [nsteps][start_stride], start_stride >= max_boxes + 1
+    size_t start_stride;    // entries; a multiple of 64 so every table is 256-byte aligned
+    float4 *force;          // [nsteps][n]
+    ug_grid_info *geo;      // [nsteps][nsims]
+};
+int run_steps(float4 *state, uint32_t *perm, const SimArgs &sa, int nsteps, uint32_t max_boxes,
+              const Workspace &w, int sweep_block, const StepSaves *saves, int32_t *status,
+              cudaStream_t s, cudaEvent_t const *events = nullptr);
+
+}  // namespace ug

@@ -1,0 +1,127 @@
+"""The library's adjoint (ug_step_backward behind a torch.autograd.Function)
+against the FP64 oracle's adjoint and against FP64 central differences."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2105_00039_gb300 import populations as P
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def U():
+    from paper_2105_00039_gb300 import ugmech
+    ugmech.load()
+    return ugmech
+
+
+def _gpu_grad(U, st, target, prm_u, steps, ckpt):
+    from paper_2105_00039_gb300.autograd import trajectory
+    x = torch.from_numpy(np.ascontiguousarray(st, np.float32)).to(DEV).requires_grad_(True)
+    k = torch.tensor(float(prm_u.k), requires_grad=True)
+    g = torch.tensor(float(prm_u.gamma), requires_grad=True)
+    out = trajectory(x, k, g, prm_u, steps, ckpt)
+    tgt = torch.from_numpy(np.asarray(target, np.float64)).to(DEV)
+    loss = ((out[:, :3].double() - tgt) ** 2).mean()
+    loss.backward()
+    return (float(loss), float(k.grad), float(g.grad), x.grad[:, :3].double().cpu().numpy(),
+            x.grad[:, 3].double().cpu().numpy())
+
+
+def _rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-30)
+
+
+def _nrel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def test_adjoint_small_with_adherence_and_cap(U):
+    from test_oracle_pins import _fd_fixture
+    st, prm = _fd_fixture(steps=3)
+    n = len(st)
+    target = st[:, :3] + 0.3 * np.sin(np.arange(3 * n).reshape(n, 3))
+    st32 = st.astype(np.float32)
+    ref = O.trajectory_grad(st32, target, prm, 3, "brute")
+    prm_u = U.Params(adherence=prm.adherence, max_disp=prm.max_disp)
+    L, dk, dg, dp, dd = _gpu_grad(U, st32, target, prm_u, 3, 2)
+    assert _rel(L, ref["loss"]) < 1e-5
+    assert _rel(dk, ref["dk"]) < TOL and _rel(dg, ref["dgamma"]) < TOL
+    assert _nrel(dp, ref["dpos"]) < TOL and _nrel(dd, ref["ddiam"]) < TOL
+
+
+def _lattice_case(side, steps):
+    st = P.lattice_cube(side, seed=5)
+    prm_t = O.Params(k=2.5, gamma=1.2, adherence=0.0)
+    target = O.trajectory(st, prm_t, steps)[:, :3]          # FP64 target trajectory
+    return st, target
+
+
+def test_adjoint_lattice_vs_oracle_and_fd(U):
+    """Differentiable workload on a 16^3 lattice: 50 steps, checkpoints every 10,
+    target from kappa=2.5, gamma=1.2; gradients at kappa=2, gamma=1."""
+    steps = 50
+    st, target = _lattice_case(16, steps)
+    prm = O.Params(adherence=0.0)
+    ref = O.trajectory_grad(st, target, prm, steps)
+    L, dk, dg, dp, dd = _gpu_grad(U, st, target, U.Params(adherence=0.0), steps, 10)
+    assert _rel(L, ref["loss"]) < 1e-4
+    assert _rel(dk, ref["dk"]) < TOL, (dk, ref["dk"])
+    assert _rel(dg, ref["dgamma"]) < TOL, (dg, ref["dgamma"])
+    assert _nrel(dp, ref["dpos"]) < TOL
+    assert _nrel(dd, ref["ddiam"]) < TOL
+    # FP64 central differences (h = 1e-3) of the oracle forward
+    h = 1e-3
+    import oracle.mech as M
+    orig = M.Params.as64
+    try:
+        M.Params.as64 = lambda self: self
+        fk = (O.trajectory_loss(st, target, O.Params(k=2.0 + h, adherence=0.0), steps)
+              - O.trajectory_loss(st, target, O.Params(k=2.0 - h, adherence=0.0), steps)) / (2 * h)
+        fg = (O.trajectory_loss(st, target, O.Params(gamma=1.0 + h, adherence=0.0), steps)
+              - O.trajectory_loss(st, target, O.Params(gamma=1.0 - h, adherence=0.0), steps)) / (2 * h)
+    finally:
+        M.Params.as64 = orig
+    assert _rel(dk, fk) < TOL, (dk, fk)
+    assert _rel(dg, fg) < TOL, (dg, fg)
+    # directional derivative along a random unit direction of the initial positions
+    v = P.random_unit_vectors(len(st), seed=9)
+    s64 = st.astype(np.float64)
+    hp = 1e-3
+    sp_, sm_ = s64.copy(), s64.copy()
+    sp_[:, :3] += hp * v
+    sm_[:, :3] -= hp * v
+    fd = (O.trajectory_loss(sp_, target, prm, steps) - O.trajectory_loss(sm_, target, prm, steps)) / (2 * hp)
+    assert _rel(float(np.sum(dp * v)), fd) < TOL, (float(np.sum(dp * v)), fd)
+
+
+@pytest.mark.skipif(os.environ.get("UG_FULL_GRAD", "0") != "1",
+                    reason="full 262,144-cell gradient check takes minutes of oracle time")
+def test_adjoint_full_size_vs_oracle(U):
+    steps = 50
+    st, target = _lattice_case(64, steps)
+    prm = O.Params(adherence=0.0)
+    ref = O.trajectory_grad(st, target, prm, steps, "kdtree")
+    L, dk, dg, dp, dd = _gpu_grad(U, st, target, U.Params(adherence=0.0), steps, 10)
+    assert _rel(dk, ref["dk"]) < TOL and _rel(dg, ref["dgamma"]) < TOL
+    assert _nrel(dp, ref["dpos"]) < TOL
+
+
+def test_backward_is_deterministic_and_zero_steps(U):
+    st = P.lattice_cube(10, seed=2)
+    x = torch.from_numpy(st).to(DEV)
+    mb = U.estimate_max_boxes(x, 0.0, slack=3.0)
+    G = torch.randn(len(st), 4, device=DEV)
+    a, ga, s1 = U.step_backward(x, U.Params(), 4, mb, G)
+    b, gb, s2 = U.step_backward(x, U.Params(), 4, mb, G)
+    U.check_status(s1)
+    U.check_status(s2)
+    assert torch.equal(a, b) and torch.equal(ga, gb)
+    c, gc, _ = U.step_backward(x, U.Params(), 0, mb, G)
+    assert torch.equal(c, G) and float(gc.abs().sum()) == 0.0

@@ -400,3 +400,14 @@ def test_planted_adjoint_mistake_is_caught(monkeypatch):
     assert check_adjoint_fd() < 1e-6
     monkeypatch.setattr(O, "trajectory_grad", bad)
     assert check_adjoint_fd() > 1e-3
+
+
+def test_sampled_form_equals_full_step():
+    st = P.jittered_lattice(4096, 16, 9.0, 1.5, 9.0, 11.0, 3)
+    prm = O.Params(contact_margin=0.5)
+    full = O.step(st, prm, method="brute")
+    idx = np.arange(0, 4096, 7)
+    smp = O.step_sampled(st, idx, prm)
+    np.testing.assert_allclose(smp["F"], full["F"][idx], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(smp["u"], full["u"][idx], rtol=0, atol=1e-13)
+    assert np.array_equal(smp["npairs"], full["npairs"][idx])
