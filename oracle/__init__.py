@@ -5,8 +5,10 @@ legs may import this package.  It shares no code with the CUDA library.
 """
 from .mech import (Params, grid, pairs_bruteforce, pairs_kdtree, find_pairs, pair_terms,
                    forces, mass, displacement, step, trajectory, trajectory_grad,
-                   trajectory_loss, mse_loss, margins, step_sampled)
+                   trajectory_loss, mse_loss, margins, step_sampled,
+                   trajectory_grad_along)
 
 __all__ = ["Params", "grid", "pairs_bruteforce", "pairs_kdtree", "find_pairs", "pair_terms",
            "forces", "mass", "displacement", "step", "trajectory", "trajectory_grad",
-           "trajectory_loss", "mse_loss", "margins", "step_sampled"]
+           "trajectory_loss", "mse_loss", "margins", "step_sampled",
+           "trajectory_grad_along"]

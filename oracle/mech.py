@@ -295,8 +295,25 @@ def trajectory_grad(state0, target_pos, prm: Params = Params(), nsteps: int = 1,
                    + sum_j (g_i - g_j) . u_ij * (1/2) dphi/dr_i,
         dphi/dr_i = (kappa - gamma R/(2 sqrt(R delta))) - gamma delta/(2 sqrt(R delta)) * r_j^2/(r_i+r_j)^2
     """
-    prm64 = prm.as64()
     final, recs = trajectory(state0, prm, nsteps, method, keep=True)
+    return _reverse(recs, final, target_pos, prm)
+
+
+def trajectory_grad_along(states, target_pos, prm: Params = Params(), method="auto"):
+    """The reverse pass of `trajectory_grad` along given forward states
+    X_0 .. X_T (for instance another implementation's float32 rows, in id
+    order): each step is linearised at the given X_t by evaluating `step` there,
+    and the loss is taken on the given X_T."""
+    recs = []
+    for X in states[:-1]:
+        X = np.asarray(X, dtype=np.float64)
+        r = step(X, prm, method)
+        recs.append(dict(state=X, **{k: v for k, v in r.items() if k != "state"}))
+    return _reverse(recs, np.asarray(states[-1], dtype=np.float64), target_pos, prm)
+
+
+def _reverse(recs, final, target_pos, prm: Params):
+    prm64 = prm.as64()
     tgt = np.asarray(target_pos, dtype=np.float64)
     n = final.shape[0]
     L = mse_loss(final[:, :3], tgt)

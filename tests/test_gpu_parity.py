@@ -70,7 +70,7 @@ def test_grid_build_with_input_ids(U):
 def test_contact_pairs_exact(U, name):
     st, margin = workloads()[name]
     srt, perm, start, info, _ = U.grid_build(_gpu(st), contact_margin=margin)
-    count, nbr = U.list_pairs(srt, start, info, margin, max_per_agent=96)
+    count, nbr = U.list_pairs(srt, start, info, margin, max_per_agent=256)
     pid = perm.cpu().numpy()
     c = count.cpu().numpy()
     nb = nbr.cpu().numpy()
@@ -174,14 +174,55 @@ def test_fused_step_is_deterministic(U):
 
 
 def test_trajectory_100_steps(U):
+    """100 independent steps on both sides, no adherence threshold (the step is
+    then continuous in the rows, so float32 and FP64 trajectories stay close)."""
     st = P.lattice_cube(16, seed=0)                    # 4096 cells, same recipe as the 1M lattice
-    prm = O.Params()
-    out, perm = _run_steps(U, st, U.Params(), 100)
+    prm = O.Params(adherence=0.0)
+    out, perm = _run_steps(U, st, U.Params(adherence=0.0), 100)
     final_g = by_id(out.astype(np.float64), perm)[:, :3]
     final_r, recs = O.trajectory(st, prm, 100, keep=True)
     mean_u = np.mean([np.linalg.norm(r["u"], axis=1).mean() for r in recs])
     err = np.linalg.norm(final_g - final_r[:, :3], axis=1) / (mean_u * 100)
     assert err.max() <= TOL_TRAJ, (err.max(), mean_u)
+
+
+def _stepwise_states(U, st, prm_u, nsteps):
+    """The GPU's rows (by id) before every step, one ug_step call per step."""
+    x = _gpu(st)
+    n = len(st)
+    mb = U.estimate_max_boxes(x, prm_u.contact_margin, slack=3.0)
+    sp = U.Stepper(n, mb, x.device)
+    perm = U.iota(n, x.device)
+    states = [st.copy()]
+    for _ in range(nsteps):
+        sp.step(x, perm, prm_u, 1)
+        states.append(U.scatter_rows(x, perm).cpu().numpy())
+    sp.check()
+    return states, mb
+
+
+def test_trajectory_100_steps_shadowed(U):
+    """With the default adherence threshold, every one of 100 steps is checked
+    against the oracle applied to the GPU's own input rows (the per-step
+    tolerance, adherence-threshold ties excluded), and the fused 100-step call
+    reproduces the step-by-step rows bit for bit."""
+    st = P.lattice_cube(16, seed=0)
+    prm = O.Params()
+    states, mb = _stepwise_states(U, st, U.Params(), 100)
+    flips_total = 0
+    for t in range(100):
+        X, Y = states[t], states[t + 1]
+        ref = O.step(X, prm)
+        flips = adherence_flips(ref["Fn"], ref["S"], prm.adherence)
+        flips_total += int(flips.sum())
+        scale = ref["S"] / O.mass(X[:, 3].astype(np.float64), prm.as64())
+        dp = np.abs(Y[:, :3].astype(np.float64) - ref["state"][:, :3])
+        ok = dp <= ulp32(Y[:, :3]) + TOL_STEP * np.maximum(np.linalg.norm(ref["u"], axis=1),
+                                                            scale)[:, None]
+        assert ok[~flips].all(), (t, np.argwhere(~ok)[:5])
+    assert flips_total <= 10
+    out, perm = _run_steps(U, st, U.Params(), 100, max_boxes=mb)
+    assert np.array_equal(by_id(out, perm), states[-1])
 
 
 def test_freeze_rule_max_disp_zero(U):

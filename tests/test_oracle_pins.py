@@ -411,3 +411,15 @@ def test_sampled_form_equals_full_step():
     np.testing.assert_allclose(smp["F"], full["F"][idx], rtol=0, atol=1e-12)
     np.testing.assert_allclose(smp["u"], full["u"][idx], rtol=0, atol=1e-13)
     assert np.array_equal(smp["npairs"], full["npairs"][idx])
+
+
+def test_reverse_pass_along_own_states_is_the_same():
+    st, prm = _fd_fixture(steps=3)
+    n = len(st)
+    target = st[:, :3] + 0.2
+    ref = O.trajectory_grad(st, target, prm, 3, "brute")
+    _, recs = O.trajectory(st, prm, 3, "brute", keep=True)
+    states = [r["state"] for r in recs] + [ref["final"]]
+    alt = O.trajectory_grad_along(states, target, prm, "brute")
+    assert alt["dk"] == ref["dk"] and alt["dgamma"] == ref["dgamma"]
+    assert np.array_equal(alt["dpos"], ref["dpos"]) and np.array_equal(alt["ddiam"], ref["ddiam"])
