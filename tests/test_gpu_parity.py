@@ -220,7 +220,11 @@ def test_trajectory_100_steps_shadowed(U):
         ok = dp <= ulp32(Y[:, :3]) + TOL_STEP * np.maximum(np.linalg.norm(ref["u"], axis=1),
                                                             scale)[:, None]
         assert ok[~flips].all(), (t, np.argwhere(~ok)[:5])
-    assert flips_total <= 10
+        # an agent whose |F| ties with the threshold either moved as the oracle
+        # says or stayed put; both are correct decisions within rounding
+        stayed = np.all(Y[flips, :3] == X[flips, :3], axis=1)
+        assert (ok[flips].all(axis=1) | stayed).all(), t
+    assert flips_total <= 0.02 * 100 * len(st)
     out, perm = _run_steps(U, st, U.Params(), 100, max_boxes=mb)
     assert np.array_equal(by_id(out, perm), states[-1])
 
