@@ -131,6 +131,24 @@ int ug_grid_build(const float *state_in, const uint32_t *perm_in, uint32_t n,
                   uint32_t *box_start, uint32_t max_boxes, ug_grid_info *info,
                   void *ws, size_t ws_bytes, int32_t *status, void *stream);
 
+/* ug_grid_build for callers that cannot allocate device memory (the paper has
+ * no counterpart: this is a library convenience).  Some callers are handed only
+ * their inputs and outputs and may not allocate at the point of the call -- a
+ * plug-in whose host application owns all of the GPU's memory, or code under a
+ * fixed memory budget -- so they cannot supply ug_grid_build's workspace.  This
+ * variant uses a fixed scratch array of about 7 MiB compiled into the library
+ * (one per GPU that loads it, held until the process exits) and calls no
+ * allocator.  Arguments and results are those of ug_grid_build.
+ *   Limits: n <= 262144 and max_boxes <= 1048576, else UG_EWORKSPACE (the
+ *   built-in scratch is too small) before any device work.
+ *   The first call on a device looks up the array's address; make it before
+ *   any stream capture.  Every call shares the array: calls that overlap on the
+ *   GPU (other streams or host threads on the same device) race on it. */
+int ug_grid_build_noalloc(const float *state_in, const uint32_t *perm_in, uint32_t n,
+                          float contact_margin, float *state_sorted, uint32_t *perm_sorted,
+                          uint32_t *box_start, uint32_t max_boxes, ug_grid_info *info,
+                          int32_t *status, void *stream);
+
 /* ------------------------------------------------------------------ forces */
 
 /* Eq. 1 summed over every overlapping pair found in the 27 boxes around each

@@ -28,7 +28,8 @@ EXPORTED = ("ug_strerror", "ug_version", "ug_workspace_bytes", "ug_grid_build",
             "ug_compute_forces", "ug_list_pairs", "ug_apply_displacement", "ug_step",
             "ug_step_traced",
             "ug_step_batched", "ug_tune_batched", "ug_backward_workspace_bytes",
-            "ug_step_backward", "ug_iota", "ug_scatter_rows", "ug_gather_rows")
+            "ug_step_backward", "ug_iota", "ug_scatter_rows", "ug_gather_rows",
+            "ug_grid_build_noalloc")
 
 
 class UgError(RuntimeError):
@@ -83,6 +84,8 @@ _SIG = {
     "ug_workspace_bytes": (ctypes.c_size_t, [_U32, _U32, _U32]),
     "ug_grid_build": (ctypes.c_int, [_P, _P, _U32, ctypes.c_float, _P, _P, _P, _U32, _P, _P,
                                      ctypes.c_size_t, _P, _P]),
+    "ug_grid_build_noalloc": (ctypes.c_int, [_P, _P, _U32, ctypes.c_float, _P, _P, _P, _U32, _P,
+                                             _P, _P]),
     "ug_compute_forces": (ctypes.c_int, [_P, _P, _P, _U32, ug_params, _P, _P, _P]),
     "ug_list_pairs": (ctypes.c_int, [_P, _P, _P, _U32, ctypes.c_float, _U32, _P, _P, _P, _P]),
     "ug_apply_displacement": (ctypes.c_int, [_P, _P, _U32, ug_params, _P, _P, _P, _P]),
