@@ -85,8 +85,10 @@ int run_steps(float4 *state, uint32_t *perm, const SimArgs &sa, int nsteps, uint
         mark(3 + 5 * t);
         launch_place(w, start, n, status, s);
         mark(4 + 5 * t);
+        // the provisional ranks are consumed by the placement kernel, so their
+        // buffer carries the sorted rows' box keys from canon to the sweep
         launch_canon(w, start, state, pcur, sorted, pnext,
-                     saves ? saves->sigma + (size_t)t * n : nullptr, n, status, s);
+                     saves ? saves->sigma + (size_t)t * n : nullptr, n, status, s, w.rank);
         mark(5 + 5 * t);
         SweepOut o{};
         o.state_out = state;
@@ -95,7 +97,7 @@ int run_steps(float4 *state, uint32_t *perm, const SimArgs &sa, int nsteps, uint
         o.geo_next = w.geo;
         o.ctrl = w.ctrl;
         o.max_boxes = max_boxes;
-        launch_sweep(kSweepStep, sorted, start, w.geo, sa, o, sweep_block, status, s);
+        launch_sweep(kSweepStep, sorted, start, w.geo, sa, o, sweep_block, status, s, w.rank);
         std::swap(pcur, pnext);
     }
     mark(1 + 5 * nsteps);
@@ -160,7 +162,7 @@ int ug_grid_build(const float *state_in, const uint32_t *perm_in, uint32_t n, fl
                   int32_t *status, void *stream) {
     if (n == 0) return UG_OK;
     if (!rows_ok(state_in) || !rows_ok(state_sorted) || !perm_sorted || !box_start || !info ||
-        !status || !ws || !aligned(ws, 256) || !aligned(box_start, 16) || max_boxes < 27 ||
+        !status || !ws || !aligned(ws, 256) || !aligned(box_start, 16) || max_boxes < 27 || max_boxes > 0x7fffff00u ||
         !(contact_margin >= 0.0f))
         return UG_EINVAL;
     Workspace w;
@@ -235,7 +237,7 @@ int ug_step(float *state, uint32_t *perm, uint32_t n, ug_params p, int32_t nstep
             uint32_t max_boxes, void *ws, size_t ws_bytes, int32_t *status, void *stream) {
     if (nsteps < 0) return UG_EINVAL;
     if (n == 0 || nsteps == 0) return UG_OK;
-    if (!rows_ok(state) || !perm || !status || !ws || !aligned(ws, 256) || max_boxes < 27 ||
+    if (!rows_ok(state) || !perm || !status || !ws || !aligned(ws, 256) || max_boxes < 27 || max_boxes > 0x7fffff00u ||
         !(p.contact_margin >= 0.0f))
         return UG_EINVAL;
     Workspace w;
@@ -254,7 +256,7 @@ int ug_step_traced(float *state, uint32_t *perm, uint32_t n, ug_params p, int32_
                    void *const *events, int32_t nevents) {
     if (nsteps < 0 || !events || nevents < 2 + 5 * nsteps) return UG_EINVAL;
     if (n == 0 || nsteps == 0) return UG_OK;
-    if (!rows_ok(state) || !perm || !status || !ws || !aligned(ws, 256) || max_boxes < 27 ||
+    if (!rows_ok(state) || !perm || !status || !ws || !aligned(ws, 256) || max_boxes < 27 || max_boxes > 0x7fffff00u ||
         !(p.contact_margin >= 0.0f))
         return UG_EINVAL;
     Workspace w;

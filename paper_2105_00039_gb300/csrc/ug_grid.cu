@@ -10,8 +10,8 @@
 //             per-simulation min/max corner and max diameter -> grid geometry
 //   k_key     box key of every row + warp-aggregated atomic histogram; the
 //             atomic's return value is a provisional rank inside the box
-//   k_scan    single-pass exclusive scan of the box counts with decoupled
-//             look-back (bounded spins), also re-zeroing the counts
+//   k_scan    single-pass exclusive scan of the box counts with a warp-wide
+//             decoupled look-back (bounded spins), also re-zeroing the counts
 //   k_place   row index -> provisional slot
 //   k_canon   stable order inside each box (rank = rows of the box with a
 //             smaller input index), gathering rows and ids into that slot
@@ -79,26 +79,34 @@ __device__ __forceinline__ void publish(unsigned long long *st, uint32_t t, uint
     *(volatile unsigned long long *)(st + t) = ((unsigned long long)flag << 32) | val;
 }
 
-__device__ uint32_t look_back(unsigned long long *st, uint32_t t, int32_t *status) {
+// Exclusive prefix of tile t from its predecessors' status words, read by one
+// warp 32 tiles at a time (lane l looks at tile t-1-l): sum tile aggregates
+// back to the nearest tile that already knows its inclusive prefix.  Waits are
+// bounded; on timeout the error is recorded and the partial sum returned so
+// that successors finish too.
+__device__ uint32_t look_back_warp(unsigned long long *st, uint32_t t, int32_t *status) {
+    const int lane = threadIdx.x & 31;
     uint32_t excl = 0;
-    int j = (int)t - 1;
+    int j = (int)t - 1 - lane;
     uint32_t spins = 0;
-    while (j >= 0) {
-        const unsigned long long w = *(volatile unsigned long long *)(st + j);
+    for (;;) {
+        const unsigned long long w =
+            j >= 0 ? *(volatile unsigned long long *)(st + j) : (2ull << 32);
         const uint32_t flag = (uint32_t)(w >> 32);
-        if (flag == 0u) {
+        if (__any_sync(kFull, flag == 0u)) {
             if (++spins > kSpinLimit || peek_status(status) != 0) {
                 set_status(status, UG_ETIMEOUT);
                 return excl;
             }
-            __nanosleep(64);
+            __nanosleep(32);
             continue;
         }
-        excl += (uint32_t)w;
-        if (flag == 2u) break;
-        --j;
+        const unsigned pmask = __ballot_sync(kFull, flag == 2u);
+        const int first = pmask ? __ffs(pmask) - 1 : 31;
+        excl += __reduce_add_sync(kFull, lane <= first ? (uint32_t)w : 0u);
+        if (pmask) return excl;
+        j -= 32;
     }
-    return excl;
 }
 
 __global__ void __launch_bounds__(kScanThreads)
@@ -145,16 +153,16 @@ k_scan(uint32_t *__restrict__ counts, uint32_t *__restrict__ start, Ctrl *ctrl,
             if (w < warp) wbase += x;
             tile_total += x;
         }
-        if (threadIdx.x == 0) {
+        if (warp == 0) {
             uint32_t excl = 0;
             if (t == 0) {
-                publish(tstat, t, 2u, tile_total);
+                if (lane == 0) publish(tstat, t, 2u, tile_total);
             } else {
-                publish(tstat, t, 1u, tile_total);
-                excl = look_back(tstat, t, status);
-                publish(tstat, t, 2u, excl + tile_total);
+                if (lane == 0) publish(tstat, t, 1u, tile_total);
+                excl = look_back_warp(tstat, t, status);
+                if (lane == 0) publish(tstat, t, 2u, excl + tile_total);
             }
-            s_prefix = excl;
+            if (lane == 0) s_prefix = excl;
         }
         __syncthreads();
         uint32_t run = s_prefix + wbase + inc - tsum;
@@ -196,7 +204,7 @@ k_canon(const uint32_t *__restrict__ tmp, const uint32_t *__restrict__ key,
         const uint32_t *__restrict__ start, const float4 *__restrict__ st_in,
         const uint32_t *__restrict__ perm_in, float4 *__restrict__ st_out,
         uint32_t *__restrict__ perm_out, uint32_t *__restrict__ sigma, uint32_t n,
-        int32_t *status) {
+        uint32_t *__restrict__ skey, int32_t *status) {
     if (cta_failed(status)) return;
     const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
@@ -209,6 +217,7 @@ k_canon(const uint32_t *__restrict__ tmp, const uint32_t *__restrict__ key,
     st_out[dest] = __ldg(st_in + id);
     perm_out[dest] = perm_in ? __ldg(perm_in + id) : id;
     if (sigma) sigma[dest] = id;
+    if (skey) skey[dest] = k;
 }
 
 // ------------------------------------------------------------------ launchers
@@ -241,9 +250,9 @@ void launch_place(const Workspace &w, const uint32_t *start, uint32_t n, int32_t
 
 void launch_canon(const Workspace &w, const uint32_t *start, const float4 *st_in,
                   const uint32_t *perm_in, float4 *st_sorted, uint32_t *perm_out, uint32_t *sigma,
-                  uint32_t n, int32_t *status, cudaStream_t s) {
+                  uint32_t n, int32_t *status, cudaStream_t s, uint32_t *skey) {
     k_canon<<<blocks_for(n, 256), 256, 0, s>>>(w.tmp, w.key, start, st_in, perm_in, st_sorted,
-                                               perm_out, sigma, n, status);
+                                               perm_out, sigma, n, skey, status);
 }
 
 }  // namespace ug

@@ -185,10 +185,10 @@ __device__ __forceinline__ bool contact(const float4 &a, float ra, const float4 
 }
 
 // ------------------------------------------------------------------ neighbour traversal
-// With boxes numbered x-fastest the 27 boxes around (bx, by, bz) are 9 runs of 3
-// consecutive boxes, one per (dy, dz); run r covers sorted slots
-// start[key(bx-1, by+dy, bz+dz)] .. start[key(bx+1, by+dy, bz+dz) + 1].
-constexpr int kListCap = 16;
+// With boxes numbered x-fastest the 27 boxes around box key k are 9 runs of 3
+// consecutive boxes, one per (dy, dz): run (dy, dz) covers sorted slots
+// start[k + dz*plane + dy*row - 1] .. start[k + dz*plane + dy*row + 2].
+constexpr int kListCap = 24;
 constexpr float kFilter = 1.0f + 1.0f / 65536.0f;
 
 __device__ __forceinline__ uint32_t run_row_key(const ug_grid_info &g, int bx, int by, int bz,
@@ -199,57 +199,81 @@ __device__ __forceinline__ uint32_t run_row_key(const ug_grid_info &g, int bx, i
 
 // Visit every candidate j != i of the 27 boxes around row i; `fn(j, row_j)` is
 // called for those passing a float32 distance filter whose 2^-16 relative band
-// keeps every true contact (the exact test is fn's job).  Candidates are
-// buffered per lane in `lst` and handed to fn in warp-converged batches.  All
-// 32 lanes of every warp must call this (invalid lanes pass valid = false).
+// keeps every true contact (the exact test is fn's job).
+//   key_i   the row's box key, or 0xffffffff to compute it from the position
+//   runs    per-thread table of the non-empty runs (9 x T entries)
+//   lst     per-thread candidate list (kListCap x T entries)
+// The runs are walked as one flattened loop (a warp's trip count is its largest
+// candidate count, not the sum of per-run maxima), the next candidate row is
+// fetched one iteration ahead, and candidates passing the filter are handed to
+// fn in warp-converged batches so that the exact, expensive path never runs
+// one lane at a time.  All 32 lanes of every warp must call this.
 template <int T, typename Fn>
 __device__ __forceinline__ void sweep_neighbours(const float4 *__restrict__ st,
                                                  const uint32_t *__restrict__ start,
                                                  const ug_grid_info &g, uint32_t i, bool valid,
-                                                 const float4 &me, float m2,
-                                                 uint32_t (*lst)[T], Fn &&fn) {
-    int bx = 1, by = 1, bz = 1;
-    int total = 0;
+                                                 const float4 &me, uint32_t key_i, float m2,
+                                                 uint2 (*runs)[T], uint32_t (*lst)[T],
+                                                 Fn &&fn) {
+    const int tid = threadIdx.x;
+    int nr = 0, total = 0;
     if (valid) {
-        box_key(me, g, bx, by, bz);
+        uint32_t key = key_i;
+        if (key == 0xffffffffu) {
+            int bx, by, bz;
+            key = box_key(me, g, bx, by, bz);
+        }
+        const int row = g.dims[0], plane = g.dims[0] * g.dims[1];
 #pragma unroll
         for (int r = 0; r < 9; ++r) {
-            const uint32_t kb = run_row_key(g, bx, by, bz, r);
-            total += (int)(__ldg(start + kb + 2) - __ldg(start + kb - 1));
+            const uint32_t kb = (uint32_t)((int)key + (r / 3 - 1) * plane + (r % 3 - 1) * row);
+            const uint32_t b = __ldg(start + kb - 1), e = __ldg(start + kb + 2);
+            if (e > b) {
+                runs[nr][tid] = make_uint2(b, e);
+                ++nr;
+                total += (int)(e - b);
+            }
         }
     }
     const float rim = 0.5f * me.w + m2;
     const int tmax = (int)__reduce_max_sync(kFull, (unsigned)total);
-    int cnt = 0;
-    int r = -1;
+    int cnt = 0, r = 0;
     uint32_t j = 0, jend = 0;
+    if (nr > 0) {
+        const uint2 c = runs[0][tid];
+        j = c.x;
+        jend = c.y;
+    }
+    float4 q = total > 0 ? __ldg(st + j) : make_float4(0.f, 0.f, 0.f, 0.f);
     auto flush = [&]() {
         const int m = (int)__reduce_max_sync(kFull, (unsigned)cnt);
         for (int k = 0; k < m; ++k) {
             if (k < cnt) {
-                const uint32_t jj = lst[k][threadIdx.x];
+                const uint32_t jj = lst[k][tid];
                 fn(jj, __ldg(st + jj));
             }
         }
         cnt = 0;
     };
     for (int t = 0; t < tmax; ++t) {
-        if (t < total) {
-            while (j >= jend) {
-                ++r;
-                const uint32_t kb = run_row_key(g, bx, by, bz, r);
-                j = __ldg(start + kb - 1);
-                jend = __ldg(start + kb + 2);
+        const bool act = t < total;
+        const float4 cur = q;
+        const uint32_t jc = j;
+        if (act) {
+            ++j;
+            if (j == jend && ++r < nr) {
+                const uint2 c = runs[r][tid];
+                j = c.x;
+                jend = c.y;
             }
-            const float4 q = __ldg(st + j);
-            const float dx = me.x - q.x, dy = me.y - q.y, dz = me.z - q.z;
+            if (t + 1 < total) q = __ldg(st + j);
+            const float dx = me.x - cur.x, dy = me.y - cur.y, dz = me.z - cur.z;
             const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            const float s = fmaf(0.5f, q.w, rim);
-            if (d2 < s * s * kFilter && j != i) {
-                lst[cnt][threadIdx.x] = j;
+            const float s = fmaf(0.5f, cur.w, rim);
+            if (d2 < s * s * kFilter && jc != i) {
+                lst[cnt][tid] = jc;
                 ++cnt;
             }
-            ++j;
         }
         if (__any_sync(kFull, cnt == kListCap)) flush();
     }
@@ -454,7 +478,7 @@ void launch_place(const Workspace &w, const uint32_t *start, uint32_t n, int32_t
                   cudaStream_t s);
 void launch_canon(const Workspace &w, const uint32_t *start, const float4 *st_in,
                   const uint32_t *perm_in, float4 *st_sorted, uint32_t *perm_out, uint32_t *sigma,
-                  uint32_t n, int32_t *status, cudaStream_t s);
+                  uint32_t n, int32_t *status, cudaStream_t s, uint32_t *skey = nullptr);
 
 // Sweep (ug_sweep.cu).
 enum SweepMode { kSweepForce = 0, kSweepStep = 1, kSweepPairs = 2 };
@@ -471,7 +495,7 @@ struct SweepOut {
 };
 void launch_sweep(int mode, const float4 *sorted, const uint32_t *start, const ug_grid_info *geo,
                   const SimArgs &sa, const SweepOut &out, int block, int32_t *status,
-                  cudaStream_t s);
+                  cudaStream_t s, const uint32_t *skey = nullptr);
 void launch_apply(const float4 *st_in, const float4 *force, uint32_t n, const ug_params &p,
                   float4 *st_out, float4 *disp_out, int32_t *status, cudaStream_t s);
 

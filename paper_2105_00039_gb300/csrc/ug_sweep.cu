@@ -29,8 +29,10 @@ namespace ug {
 template <int MODE, int T>
 __global__ void __launch_bounds__(T)
 k_sweep(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
-        const ug_grid_info *__restrict__ geo, SimArgs sa, SweepOut out, int32_t *status) {
+        const ug_grid_info *__restrict__ geo, const uint32_t *__restrict__ skey, SimArgs sa,
+        SweepOut out, int32_t *status) {
     __shared__ uint32_t lst[kListCap][T];
+    __shared__ uint2 runs[9][T];
     if (cta_failed(status)) return;
     const uint32_t first = blockIdx.x * T;
     const uint32_t i = first + threadIdx.x;
@@ -45,7 +47,9 @@ k_sweep(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     const float ri = 0.5f * me.w;
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
     uint32_t np = 0;
-    sweep_neighbours<T>(st, start, g, i, valid, me, m2, lst, [&](uint32_t jj, const float4 &q) {
+    const uint32_t key_i = (skey != nullptr && valid) ? __ldg(skey + i) : 0xffffffffu;
+    sweep_neighbours<T>(st, start, g, i, valid, me, key_i, m2, runs, lst,
+                        [&](uint32_t jj, const float4 &q) {
         ContactGeo c;
         if (!contact(me, ri, q, m2, c)) return;
         if (MODE == kSweepPairs) {
@@ -92,26 +96,31 @@ k_sweep(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
 template <int MODE>
 static void launch_mode(const float4 *sorted, const uint32_t *start, const ug_grid_info *geo,
                         const SimArgs &sa, const SweepOut &out, int block, int32_t *status,
-                        cudaStream_t s) {
+                        cudaStream_t s, const uint32_t *skey) {
     switch (block) {
     case 64:
-        k_sweep<MODE, 64><<<(sa.n + 63) / 64, 64, 0, s>>>(sorted, start, geo, sa, out, status);
+        k_sweep<MODE, 64><<<(sa.n + 63) / 64, 64, 0, s>>>(sorted, start, geo, skey, sa, out, status);
         break;
     case 256:
-        k_sweep<MODE, 256><<<(sa.n + 255) / 256, 256, 0, s>>>(sorted, start, geo, sa, out, status);
+        k_sweep<MODE, 256><<<(sa.n + 255) / 256, 256, 0, s>>>(sorted, start, geo, skey, sa, out,
+                                                             status);
         break;
     default:
-        k_sweep<MODE, 128><<<(sa.n + 127) / 128, 128, 0, s>>>(sorted, start, geo, sa, out, status);
+        k_sweep<MODE, 128><<<(sa.n + 127) / 128, 128, 0, s>>>(sorted, start, geo, skey, sa, out,
+                                                             status);
         break;
     }
 }
 
 void launch_sweep(int mode, const float4 *sorted, const uint32_t *start, const ug_grid_info *geo,
                   const SimArgs &sa, const SweepOut &out, int block, int32_t *status,
-                  cudaStream_t s) {
-    if (mode == kSweepForce) launch_mode<kSweepForce>(sorted, start, geo, sa, out, block, status, s);
-    else if (mode == kSweepStep) launch_mode<kSweepStep>(sorted, start, geo, sa, out, block, status, s);
-    else launch_mode<kSweepPairs>(sorted, start, geo, sa, out, block, status, s);
+                  cudaStream_t s, const uint32_t *skey) {
+    if (mode == kSweepForce)
+        launch_mode<kSweepForce>(sorted, start, geo, sa, out, block, status, s, skey);
+    else if (mode == kSweepStep)
+        launch_mode<kSweepStep>(sorted, start, geo, sa, out, block, status, s, skey);
+    else
+        launch_mode<kSweepPairs>(sorted, start, geo, sa, out, block, status, s, skey);
 }
 
 // ------------------------------------------------------------------ standalone move
