@@ -149,12 +149,22 @@ struct ContactGeo {
     float rb;      // radius of b
     float rsum;    // ra + rb (rounded)
 };
-__device__ __forceinline__ bool contact(const float4 &a, float ra, const float4 &b, float m2,
-                                        ContactGeo &c) {
-    float lx, ly, lz;
-    two_sum(a.x, -b.x, c.hx, lx);
-    two_sum(a.y, -b.y, c.hy, ly);
-    two_sum(a.z, -b.z, c.hz, lz);
+// EXACT_DIFF = false assumes p_a - p_b is exact in float32, which holds by
+// Sterbenz's lemma when |coordinate of a| >= 3 e on every axis and |p_a - p_b|
+// is below the box edge e (see far_from_origin); the residual terms are then 0.
+template <bool EXACT_DIFF>
+__device__ __forceinline__ bool contact_t(const float4 &a, float ra, const float4 &b, float m2,
+                                          ContactGeo &c) {
+    float lx = 0.f, ly = 0.f, lz = 0.f;
+    if (EXACT_DIFF) {
+        two_sum(a.x, -b.x, c.hx, lx);
+        two_sum(a.y, -b.y, c.hy, ly);
+        two_sum(a.z, -b.z, c.hz, lz);
+    } else {
+        c.hx = __fsub_rn(a.x, b.x);
+        c.hy = __fsub_rn(a.y, b.y);
+        c.hz = __fsub_rn(a.z, b.z);
+    }
     float px, ex, py, ey, pz, ez;
     two_prod(c.hx, c.hx, px, ex);
     two_prod(c.hy, c.hy, py, ey);
@@ -162,7 +172,8 @@ __device__ __forceinline__ bool contact(const float4 &a, float ra, const float4 
     float s1, e1, D, e2;
     two_sum(px, py, s1, e1);
     two_sum(s1, pz, D, e2);
-    const float E = ex + ey + ez + e1 + e2 + 2.0f * (c.hx * lx + c.hy * ly + c.hz * lz);
+    float E = ex + ey + ez + e1 + e2;
+    if (EXACT_DIFF) E += 2.0f * (c.hx * lx + c.hy * ly + c.hz * lz);
     c.rb = 0.5f * b.w;
     float sh, sl;
     two_sum(ra, c.rb, sh, sl);
@@ -183,12 +194,21 @@ __device__ __forceinline__ bool contact(const float4 &a, float ra, const float4 
     c.delta = __fdividef(q, sh + d);
     return true;
 }
+__device__ __forceinline__ bool contact(const float4 &a, float ra, const float4 &b, float m2,
+                                        ContactGeo &c) {
+    return contact_t<true>(a, ra, b, m2, c);
+}
+// True when every float32 difference p_a - p_b with |p_a - p_b| < e is exact.
+__device__ __forceinline__ bool far_from_origin(const float4 &a, float e) {
+    const float lim = 3.0f * e;
+    return fabsf(a.x) >= lim && fabsf(a.y) >= lim && fabsf(a.z) >= lim;
+}
 
 // ------------------------------------------------------------------ neighbour traversal
 // With boxes numbered x-fastest the 27 boxes around box key k are 9 runs of 3
 // consecutive boxes, one per (dy, dz): run (dy, dz) covers sorted slots
 // start[k + dz*plane + dy*row - 1] .. start[k + dz*plane + dy*row + 2].
-constexpr int kListCap = 24;
+constexpr int kListCap = 20;
 constexpr float kFilter = 1.0f + 1.0f / 65536.0f;
 
 __device__ __forceinline__ uint32_t run_row_key(const ug_grid_info &g, int bx, int by, int bz,
@@ -203,11 +223,14 @@ __device__ __forceinline__ uint32_t run_row_key(const ug_grid_info &g, int bx, i
 //   key_i   the row's box key, or 0xffffffff to compute it from the position
 //   runs    per-thread table of the non-empty runs (9 x T entries)
 //   lst     per-thread candidate list (kListCap x T entries)
-// The runs are walked as one flattened loop (a warp's trip count is its largest
-// candidate count, not the sum of per-run maxima), the next candidate row is
-// fetched one iteration ahead, and candidates passing the filter are handed to
-// fn in warp-converged batches so that the exact, expensive path never runs
-// one lane at a time.  All 32 lanes of every warp must call this.
+// The runs are walked as one flattened loop, so a warp's trip count is its
+// largest candidate count rather than the sum of per-run maxima.  A lane that
+// has run out of candidates keeps re-reading its own row, which the j != i test
+// rejects, so the loop body needs no per-lane exit branch; it is unrolled by 4
+// with one warp vote per 4 candidates, and the next candidate row is always
+// fetched one step ahead.  Candidates passing the filter are handed to fn in
+// warp-converged batches so that the exact, expensive path never runs one lane
+// at a time.  All 32 lanes of every warp must call this.
 template <int T, typename Fn>
 __device__ __forceinline__ void sweep_neighbours(const float4 *__restrict__ st,
                                                  const uint32_t *__restrict__ start,
@@ -215,6 +238,7 @@ __device__ __forceinline__ void sweep_neighbours(const float4 *__restrict__ st,
                                                  const float4 &me, uint32_t key_i, float m2,
                                                  uint2 (*runs)[T], uint32_t (*lst)[T],
                                                  Fn &&fn) {
+    constexpr int kUnroll = 4;
     const int tid = threadIdx.x;
     int nr = 0, total = 0;
     if (valid) {
@@ -235,16 +259,17 @@ __device__ __forceinline__ void sweep_neighbours(const float4 *__restrict__ st,
             }
         }
     }
+    const uint32_t self = valid ? i : 0u;
     const float rim = 0.5f * me.w + m2;
     const int tmax = (int)__reduce_max_sync(kFull, (unsigned)total);
     int cnt = 0, r = 0;
-    uint32_t j = 0, jend = 0;
+    uint32_t j = self, jend = self + 1;
     if (nr > 0) {
         const uint2 c = runs[0][tid];
         j = c.x;
         jend = c.y;
     }
-    float4 q = total > 0 ? __ldg(st + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 q = __ldg(st + j);
     auto flush = [&]() {
         const int m = (int)__reduce_max_sync(kFull, (unsigned)cnt);
         for (int k = 0; k < m; ++k) {
@@ -255,27 +280,33 @@ __device__ __forceinline__ void sweep_neighbours(const float4 *__restrict__ st,
         }
         cnt = 0;
     };
-    for (int t = 0; t < tmax; ++t) {
-        const bool act = t < total;
-        const float4 cur = q;
-        const uint32_t jc = j;
-        if (act) {
+    for (int t = 0; t < tmax; t += kUnroll) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const float4 cur = q;
+            const uint32_t jc = j;
             ++j;
-            if (j == jend && ++r < nr) {
-                const uint2 c = runs[r][tid];
-                j = c.x;
-                jend = c.y;
+            if (j == jend) {
+                ++r;
+                if (r < nr) {
+                    const uint2 c = runs[r][tid];
+                    j = c.x;
+                    jend = c.y;
+                } else {
+                    j = self;
+                    jend = self + 1;
+                }
             }
-            if (t + 1 < total) q = __ldg(st + j);
+            q = __ldg(st + j);
             const float dx = me.x - cur.x, dy = me.y - cur.y, dz = me.z - cur.z;
             const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
             const float s = fmaf(0.5f, cur.w, rim);
-            if (d2 < s * s * kFilter && jc != i) {
+            if (d2 < s * s * kFilter && jc != self) {
                 lst[cnt][tid] = jc;
                 ++cnt;
             }
         }
-        if (__any_sync(kFull, cnt == kListCap)) flush();
+        if (__any_sync(kFull, cnt > kListCap - kUnroll)) flush();
     }
     flush();
 }

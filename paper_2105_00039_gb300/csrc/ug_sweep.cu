@@ -48,10 +48,15 @@ k_sweep(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
     uint32_t np = 0;
     const uint32_t key_i = (skey != nullptr && valid) ? __ldg(skey + i) : 0xffffffffu;
+    // filtered candidates lie within e (+ rounding) of row i: if every lane of
+    // the warp is far from the coordinate planes their differences are exact
+    const bool exact_diffs = __all_sync(kFull, !valid || far_from_origin(me, g.edge));
     sweep_neighbours<T>(st, start, g, i, valid, me, key_i, m2, runs, lst,
                         [&](uint32_t jj, const float4 &q) {
         ContactGeo c;
-        if (!contact(me, ri, q, m2, c)) return;
+        const bool hit = exact_diffs ? contact_t<false>(me, ri, q, m2, c)
+                                     : contact_t<true>(me, ri, q, m2, c);
+        if (!hit) return;
         if (MODE == kSweepPairs) {
             if (np < out.max_per_agent) out.nbr[(size_t)i * out.max_per_agent + np] = jj;
         } else {
