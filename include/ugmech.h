@@ -100,7 +100,7 @@ typedef struct {
 
 /* Launch tuning for the batched step (autotuned by ug_tune_batched). */
 typedef struct {
-    int32_t sweep_block; /* threads per CTA of the force sweep: 64, 128 or 256; 0 = default */
+    int32_t sweep_block; /* threads per CTA of the force sweep: 64 or 128; 0 = default (128) */
     int32_t reserved[7];
 } ug_tuning;
 

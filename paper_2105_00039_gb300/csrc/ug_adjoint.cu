@@ -107,8 +107,7 @@ k_adj_sweep(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
             const ug_grid_info *__restrict__ geo, const float4 *__restrict__ g,
             const float4 *__restrict__ W, const uint32_t *__restrict__ sigma, uint32_t n,
             ug_params P, float4 *__restrict__ Gout, float4 *partial, int32_t *status) {
-    __shared__ uint32_t lst[kListCap][kAdjT];
-    __shared__ uint2 runs[9][kAdjT];
+    __shared__ WarpLists wl[kAdjT / 32];
     __shared__ float s_red[2][kAdjT / 32];
     if (cta_failed(status)) return;
     const uint32_t i = blockIdx.x * kAdjT + threadIdx.x;
@@ -119,7 +118,7 @@ k_adj_sweep(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     const float4 gi = valid ? __ldg(g + i) : make_float4(0.f, 0.f, 0.f, 0.f);
     const float ri = 0.5f * me.w;
     float ax = 0.f, ay = 0.f, az = 0.f, ad = 0.f, pk = 0.f, pg = 0.f;
-    sweep_neighbours<kAdjT>(st, start, gi_geo, i, valid, me, 0xffffffffu, m2, runs, lst,
+    sweep_neighbours(st, start, gi_geo, i, valid, me, 0xffffffffu, m2, wl[threadIdx.x >> 5],
                             [&](uint32_t jj, const float4 &q) {
         ContactGeo c;
         if (!contact(me, ri, q, m2, c)) return;

@@ -289,7 +289,7 @@ int ug_step_batched(float *state, uint32_t *perm, const uint32_t *sim_offset, ui
     sa.n = n_total;
     sa.bounds_copies = bounds_copies(nsims);
     int block = tuning && tuning->sweep_block ? tuning->sweep_block : 128;
-    if (block != 64 && block != 128 && block != 256) return UG_EINVAL;
+    if (block != 64 && block != 128) return UG_EINVAL;
     return run_steps(reinterpret_cast<float4 *>(state), perm, sa, nsteps, max_boxes, w, block,
                      nullptr, status, static_cast<cudaStream_t>(stream));
 }
@@ -329,10 +329,10 @@ int ug_tune_batched(const float *state, const uint32_t *sim_offset, uint32_t nsi
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return UG_ECUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return UG_ECUDA; }
-    const int cands[3] = {64, 128, 256};
+    const int cands[2] = {64, 128};
     float best_ms = 1e30f;
     int rc = UG_OK;
-    for (int c = 0; c < 3 && rc == UG_OK; ++c) {
+    for (int c = 0; c < 2 && rc == UG_OK; ++c) {
         SweepOut o{};
         o.force = force;
         launch_sweep(kSweepForce, w.sorted, w.start, w.geo, sa, o, cands[c], status, s);   // warm

@@ -221,8 +221,7 @@ __device__ __forceinline__ uint32_t run_row_key(const ug_grid_info &g, int bx, i
 // called for those passing a float32 distance filter whose 2^-16 relative band
 // keeps every true contact (the exact test is fn's job).
 //   key_i   the row's box key, or 0xffffffff to compute it from the position
-//   runs    per-thread table of the non-empty runs (9 x T entries)
-//   lst     per-thread candidate list (kListCap x T entries)
+//   w       this warp's run table (non-empty runs) and candidate lists
 // The runs are walked as one flattened loop, so a warp's trip count is its
 // largest candidate count rather than the sum of per-run maxima.  A lane that
 // has run out of candidates keeps re-reading its own row, which the j != i test
@@ -231,15 +230,21 @@ __device__ __forceinline__ uint32_t run_row_key(const ug_grid_info &g, int bx, i
 // fetched one step ahead.  Candidates passing the filter are handed to fn in
 // warp-converged batches so that the exact, expensive path never runs one lane
 // at a time.  All 32 lanes of every warp must call this.
-template <int T, typename Fn>
+struct WarpLists {            // per-warp scratch of sweep_neighbours (shared memory)
+    uint2 runs[9][32];
+    uint32_t lst[kListCap][32];
+};
+
+template <typename Fn>
 __device__ __forceinline__ void sweep_neighbours(const float4 *__restrict__ st,
                                                  const uint32_t *__restrict__ start,
                                                  const ug_grid_info &g, uint32_t i, bool valid,
                                                  const float4 &me, uint32_t key_i, float m2,
-                                                 uint2 (*runs)[T], uint32_t (*lst)[T],
-                                                 Fn &&fn) {
+                                                 WarpLists &w, Fn &&fn) {
     constexpr int kUnroll = 4;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x & 31;
+    auto &runs = w.runs;
+    auto &lst = w.lst;
     int nr = 0, total = 0;
     if (valid) {
         uint32_t key = key_i;

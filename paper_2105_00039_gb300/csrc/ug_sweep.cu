@@ -26,13 +26,162 @@
 
 namespace ug {
 
+// ------------------------------------------------------------------ staged traversal
+// A warp's 32 consecutive agents lie in one to a few rows of boxes.  For each of
+// those rows (at most kStageMaxRows) the warp copies the 9 neighbouring row
+// segments that cover its agents' neighbourhoods, boxes [x_lo - 1, x_hi + 1],
+// from the sorted rows into shared memory with coalesced cp.async, then every
+// lane walks its own 9 runs inside the staged copy.  Returns false (nothing
+// done) when the staged rows would not fit; the caller then walks global memory.
+constexpr int kStageRows = 384;
+constexpr int kStageList = 20;
+constexpr int kStageMaxRows = 3;
+
+struct WarpStaged {
+    float4 rows[kStageRows];
+    uint32_t runs[9][32];            // begin | end << 16, offsets into rows
+    uint16_t lst[kStageList][32];
+};
+union WarpSmem {
+    WarpLists gl;
+    WarpStaged sg;
+};
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+template <typename Fn>
+__device__ __forceinline__ bool sweep_staged(const float4 *__restrict__ st,
+                                             const uint32_t *__restrict__ start,
+                                             const ug_grid_info &g, uint32_t i, bool valid,
+                                             const float4 &me_in, uint32_t key, float m2,
+                                             WarpStaged &w, Fn &&fn) {
+    constexpr int kUnroll = 4;
+    const int lane = threadIdx.x & 31;
+    const unsigned vmask = __ballot_sync(kFull, valid);
+    if (vmask == 0u) return true;
+    const int last_valid = 31 - __clz(vmask);
+    const uint32_t dx = (uint32_t)g.dims[0];
+    // invalid lanes (past n) take the last valid lane's box so that they add no row
+    const uint32_t k = __shfl_sync(kFull, key, valid ? lane : last_valid);
+    const uint32_t rel = k - g.box_base;
+    const uint32_t row = rel / dx;
+    const int bx = (int)(rel - row * dx);
+    const uint32_t prev = __shfl_up_sync(kFull, row, 1);
+    const unsigned heads = __ballot_sync(kFull, lane == 0 || prev != row);
+    const int R = __popc(heads);
+    if (R > kStageMaxRows) return false;
+    const int myrow = __popc(heads & (0xffffffffu >> (31 - lane))) - 1;
+    // lane s < 9R describes segment s = (warp row s / 9, neighbour row s % 9)
+    const int sk = min(lane / 9, R - 1), sm = lane % 9;
+    const int hl = (int)__fns(heads, 0, sk + 1);
+    const int ll = sk + 1 < R ? (int)__fns(heads, 0, sk + 2) - 1 : last_valid;
+    const uint32_t srow = __shfl_sync(kFull, row, hl);
+    const int lo = __shfl_sync(kFull, bx, hl), hi = __shfl_sync(kFull, bx, ll);
+    uint32_t sbeg = 0, slen = 0;
+    if (lane < 9 * R) {
+        const int dz = sm / 3 - 1, dy = sm % 3 - 1;
+        const uint32_t kr = g.box_base + (uint32_t)((int)srow + dz * g.dims[1] + dy) * dx;
+        sbeg = __ldg(start + kr + lo - 1);
+        slen = __ldg(start + kr + hi + 2) - sbeg;
+    }
+    uint32_t soff = slen;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, soff, o);
+        if (lane >= o) soff += y;
+    }
+    const uint32_t total_rows = __shfl_sync(kFull, soff, 31);
+    soff -= slen;
+    if (total_rows > (uint32_t)kStageRows) return false;
+    for (int sg = 0; sg < 9 * R; ++sg) {
+        const uint32_t b = __shfl_sync(kFull, sbeg, sg), o = __shfl_sync(kFull, soff, sg);
+        const uint32_t L = __shfl_sync(kFull, slen, sg);
+        for (uint32_t q = lane; q < L; q += 32) cp_async16(&w.rows[o + q], st + b + q);
+    }
+    // this lane's runs, as offsets into the staged rows
+    const float4 me = valid ? me_in : make_float4(1e30f, 1e30f, 1e30f, 1.f);
+    int nr = 0, total = 0;
+    uint32_t self = 0;
+    const int plane = g.dims[0] * g.dims[1];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+        const int sg = myrow * 9 + r;
+        const uint32_t b = __shfl_sync(kFull, sbeg, sg), o = __shfl_sync(kFull, soff, sg);
+        if (valid) {
+            const uint32_t kb = (uint32_t)((int)key + (r / 3 - 1) * plane + (r % 3 - 1) * (int)dx);
+            const uint32_t rb = __ldg(start + kb - 1), re = __ldg(start + kb + 2);
+            if (r == 4) self = o + (i - b);
+            if (re > rb) {
+                w.runs[nr][lane] = (o + (rb - b)) | ((o + (re - b)) << 16);
+                ++nr;
+                total += (int)(re - rb);
+            }
+        }
+    }
+    cp_async_wait_all();
+    __syncwarp();
+    const float rim = 0.5f * me.w + m2;
+    const int tmax = (int)__reduce_max_sync(kFull, (unsigned)total);
+    int cnt = 0, r = 0;
+    uint32_t j = self, jend = self + 1;
+    if (nr > 0) {
+        const uint32_t c = w.runs[0][lane];
+        j = c & 0xffffu;
+        jend = c >> 16;
+    }
+    float4 q = w.rows[j];
+    auto flush = [&]() {
+        const int m = (int)__reduce_max_sync(kFull, (unsigned)cnt);
+        for (int kk = 0; kk < m; ++kk) {
+            if (kk < cnt) fn(w.rows[w.lst[kk][lane]]);
+        }
+        cnt = 0;
+    };
+    for (int t = 0; t < tmax; t += kUnroll) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const float4 cur = q;
+            const uint32_t jc = j;
+            ++j;
+            if (j == jend) {
+                ++r;
+                if (r < nr) {
+                    const uint32_t c = w.runs[r][lane];
+                    j = c & 0xffffu;
+                    jend = c >> 16;
+                } else {
+                    j = self;
+                    jend = self + 1;
+                }
+            }
+            q = w.rows[j];
+            const float ddx = me.x - cur.x, ddy = me.y - cur.y, ddz = me.z - cur.z;
+            const float d2 = fmaf(ddz, ddz, fmaf(ddy, ddy, ddx * ddx));
+            const float s = fmaf(0.5f, cur.w, rim);
+            if (d2 < s * s * kFilter && jc != self) {
+                w.lst[cnt][lane] = (uint16_t)jc;
+                ++cnt;
+            }
+        }
+        if (__any_sync(kFull, cnt > kStageList - kUnroll)) flush();
+    }
+    flush();
+    __syncwarp();
+    return true;
+}
+
 template <int MODE, int T>
 __global__ void __launch_bounds__(T)
 k_sweep(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
         const ug_grid_info *__restrict__ geo, const uint32_t *__restrict__ skey, SimArgs sa,
         SweepOut out, int32_t *status) {
-    __shared__ uint32_t lst[kListCap][T];
-    __shared__ uint2 runs[9][T];
+    __shared__ WarpSmem wsm[T / 32];
     if (cta_failed(status)) return;
     const uint32_t first = blockIdx.x * T;
     const uint32_t i = first + threadIdx.x;
@@ -42,24 +191,21 @@ k_sweep(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     const ug_params P = sim_params(sa, sim);
     const ug_grid_info g = geo[sim];
     const float m2 = 2.0f * P.contact_margin;
+    WarpSmem &ws = wsm[threadIdx.x >> 5];
 
     const float4 me = valid ? __ldg(st + i) : make_float4(0.f, 0.f, 0.f, 1.f);
     const float ri = 0.5f * me.w;
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
     uint32_t np = 0;
-    const uint32_t key_i = (skey != nullptr && valid) ? __ldg(skey + i) : 0xffffffffu;
     // filtered candidates lie within e (+ rounding) of row i: if every lane of
     // the warp is far from the coordinate planes their differences are exact
     const bool exact_diffs = __all_sync(kFull, !valid || far_from_origin(me, g.edge));
-    sweep_neighbours<T>(st, start, g, i, valid, me, key_i, m2, runs, lst,
-                        [&](uint32_t jj, const float4 &q) {
+    auto on_candidate = [&](const float4 &q) -> bool {
         ContactGeo c;
         const bool hit = exact_diffs ? contact_t<false>(me, ri, q, m2, c)
                                      : contact_t<true>(me, ri, q, m2, c);
-        if (!hit) return;
-        if (MODE == kSweepPairs) {
-            if (np < out.max_per_agent) out.nbr[(size_t)i * out.max_per_agent + np] = jj;
-        } else {
+        if (!hit) return false;
+        if (MODE != kSweepPairs) {
             const float R = __fdividef(ri * c.rb, c.rsum);
             const float rd = R * c.delta;
             const float root = rd * rsqrtf(rd);
@@ -70,7 +216,34 @@ k_sweep(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
             comp_add(sz, cz, coef * c.hz);
         }
         ++np;
-    });
+        return true;
+    };
+    bool done = false;
+    // a warp spanning two simulations walks global memory (batched boundaries)
+    const bool warp_one_sim = uniform || __all_sync(kFull, find_sim(sa, min(i, sa.n - 1)) == sim);
+    if (MODE != kSweepPairs && warp_one_sim) {
+        uint32_t key_i = 0u;
+        if (valid) {
+            if (skey != nullptr) {
+                key_i = __ldg(skey + i);
+            } else {
+                int bx, by, bz;
+                key_i = box_key(me, g, bx, by, bz);
+            }
+        }
+        done = sweep_staged(st, start, g, i, valid, me, key_i, m2, ws.sg,
+                            [&](const float4 &q) { on_candidate(q); });
+    }
+    if (!done) {
+        const uint32_t key_i = (skey != nullptr && valid) ? __ldg(skey + i) : 0xffffffffu;
+        sweep_neighbours(st, start, g, i, valid, me, key_i, m2, ws.gl,
+                         [&](uint32_t jj, const float4 &q) {
+            const uint32_t before = np;
+            on_candidate(q);
+            if (MODE == kSweepPairs && np != before && before < out.max_per_agent)
+                out.nbr[(size_t)i * out.max_per_agent + before] = jj;
+        });
+    }
 
     if (MODE == kSweepPairs) {
         if (valid) {
@@ -102,19 +275,11 @@ template <int MODE>
 static void launch_mode(const float4 *sorted, const uint32_t *start, const ug_grid_info *geo,
                         const SimArgs &sa, const SweepOut &out, int block, int32_t *status,
                         cudaStream_t s, const uint32_t *skey) {
-    switch (block) {
-    case 64:
+    if (block == 64)
         k_sweep<MODE, 64><<<(sa.n + 63) / 64, 64, 0, s>>>(sorted, start, geo, skey, sa, out, status);
-        break;
-    case 256:
-        k_sweep<MODE, 256><<<(sa.n + 255) / 256, 256, 0, s>>>(sorted, start, geo, skey, sa, out,
-                                                             status);
-        break;
-    default:
+    else
         k_sweep<MODE, 128><<<(sa.n + 127) / 128, 128, 0, s>>>(sorted, start, geo, skey, sa, out,
                                                              status);
-        break;
-    }
 }
 
 void launch_sweep(int mode, const float4 *sorted, const uint32_t *start, const ug_grid_info *geo,
