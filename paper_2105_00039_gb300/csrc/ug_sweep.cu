@@ -220,7 +220,7 @@ k_sweep(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     };
     bool done = false;
     // a warp spanning two simulations walks global memory (batched boundaries)
-    const bool warp_one_sim = uniform || __all_sync(kFull, find_sim(sa, min(i, sa.n - 1)) == sim);
+    const bool warp_one_sim = uniform || __all_sync(kFull, sim == __shfl_sync(kFull, sim, 0));
     if (MODE != kSweepPairs && warp_one_sim) {
         uint32_t key_i = 0u;
         if (valid) {
