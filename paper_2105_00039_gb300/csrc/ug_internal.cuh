@@ -221,17 +221,16 @@ __device__ __forceinline__ uint32_t run_row_key(const ug_grid_info &g, int bx, i
 // called for those passing a float32 distance filter whose 2^-16 relative band
 // keeps every true contact (the exact test is fn's job).
 //   key_i   the row's box key, or 0xffffffff to compute it from the position
-//   w       this warp's run table (non-empty runs) and candidate lists
-// The runs are walked as one flattened loop, so a warp's trip count is its
-// largest candidate count rather than the sum of per-run maxima.  A lane that
-// has run out of candidates keeps re-reading its own row, which the j != i test
-// rejects, so the loop body needs no per-lane exit branch; it is unrolled by 4
-// with one warp vote per 4 candidates, and the next candidate row is always
-// fetched one step ahead.  Candidates passing the filter are handed to fn in
+//   w       this warp's candidate lists
+// The 9 runs are visited one after another; inside a run every lane tests its
+// t-th candidate in lockstep (trip count = the warp's longest run), with the
+// index clamped into the lane's run and the result masked, so the loop body
+// has no divergent branch.  Candidates passing the filter are handed to fn in
 // warp-converged batches so that the exact, expensive path never runs one lane
 // at a time.  All 32 lanes of every warp must call this.
+constexpr int kSweepUnroll = 2;
+
 struct WarpLists {            // per-warp scratch of sweep_neighbours (shared memory)
-    uint2 runs[9][32];
     uint32_t lst[kListCap][32];
 };
 
@@ -241,77 +240,56 @@ __device__ __forceinline__ void sweep_neighbours(const float4 *__restrict__ st,
                                                  const ug_grid_info &g, uint32_t i, bool valid,
                                                  const float4 &me, uint32_t key_i, float m2,
                                                  WarpLists &w, Fn &&fn) {
-    constexpr int kUnroll = 4;
-    const int tid = threadIdx.x & 31;
-    auto &runs = w.runs;
-    auto &lst = w.lst;
-    int nr = 0, total = 0;
+    const int lane = threadIdx.x & 31;
+    uint32_t key = 0;
     if (valid) {
-        uint32_t key = key_i;
+        key = key_i;
         if (key == 0xffffffffu) {
             int bx, by, bz;
             key = box_key(me, g, bx, by, bz);
         }
-        const int row = g.dims[0], plane = g.dims[0] * g.dims[1];
-#pragma unroll
-        for (int r = 0; r < 9; ++r) {
-            const uint32_t kb = (uint32_t)((int)key + (r / 3 - 1) * plane + (r % 3 - 1) * row);
-            const uint32_t b = __ldg(start + kb - 1), e = __ldg(start + kb + 2);
-            if (e > b) {
-                runs[nr][tid] = make_uint2(b, e);
-                ++nr;
-                total += (int)(e - b);
-            }
-        }
     }
+    const int row = g.dims[0], plane = g.dims[0] * g.dims[1];
     const uint32_t self = valid ? i : 0u;
     const float rim = 0.5f * me.w + m2;
-    const int tmax = (int)__reduce_max_sync(kFull, (unsigned)total);
-    int cnt = 0, r = 0;
-    uint32_t j = self, jend = self + 1;
-    if (nr > 0) {
-        const uint2 c = runs[0][tid];
-        j = c.x;
-        jend = c.y;
-    }
-    float4 q = __ldg(st + j);
+    int cnt = 0;
     auto flush = [&]() {
         const int m = (int)__reduce_max_sync(kFull, (unsigned)cnt);
         for (int k = 0; k < m; ++k) {
             if (k < cnt) {
-                const uint32_t jj = lst[k][tid];
+                const uint32_t jj = w.lst[k][lane];
                 fn(jj, __ldg(st + jj));
             }
         }
         cnt = 0;
     };
-    for (int t = 0; t < tmax; t += kUnroll) {
+#pragma unroll 1
+    for (int r = 0; r < 9; ++r) {
+        uint32_t b = self;
+        int len = 0;
+        if (valid) {
+            const uint32_t kb = (uint32_t)((int)key + (r / 3 - 1) * plane + (r % 3 - 1) * row);
+            b = __ldg(start + kb - 1);
+            len = (int)(__ldg(start + kb + 2) - b);
+            if (len == 0) b = self;
+        }
+        const int last = max(len - 1, 0);
+        const int lmax = (int)__reduce_max_sync(kFull, (unsigned)len);
+        for (int t = 0; t < lmax; t += kSweepUnroll) {
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const float4 cur = q;
-            const uint32_t jc = j;
-            ++j;
-            if (j == jend) {
-                ++r;
-                if (r < nr) {
-                    const uint2 c = runs[r][tid];
-                    j = c.x;
-                    jend = c.y;
-                } else {
-                    j = self;
-                    jend = self + 1;
+            for (int u = 0; u < kSweepUnroll; ++u) {
+                const uint32_t jc = b + (uint32_t)min(t + u, last);
+                const float4 cur = __ldg(st + jc);
+                const float dx = me.x - cur.x, dy = me.y - cur.y, dz = me.z - cur.z;
+                const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                const float s = fmaf(0.5f, cur.w, rim);
+                if ((t + u < len) & (jc != self) & (d2 < s * s * kFilter)) {
+                    w.lst[cnt][lane] = jc;
+                    ++cnt;
                 }
             }
-            q = __ldg(st + j);
-            const float dx = me.x - cur.x, dy = me.y - cur.y, dz = me.z - cur.z;
-            const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            const float s = fmaf(0.5f, cur.w, rim);
-            if (d2 < s * s * kFilter && jc != self) {
-                lst[cnt][tid] = jc;
-                ++cnt;
-            }
+            if (__any_sync(kFull, cnt > kListCap - kSweepUnroll)) flush();
         }
-        if (__any_sync(kFull, cnt > kListCap - kUnroll)) flush();
     }
     flush();
 }

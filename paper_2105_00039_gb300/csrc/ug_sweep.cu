@@ -61,7 +61,6 @@ __device__ __forceinline__ bool sweep_staged(const float4 *__restrict__ st,
                                              const ug_grid_info &g, uint32_t i, bool valid,
                                              const float4 &me_in, uint32_t key, float m2,
                                              WarpStaged &w, Fn &&fn) {
-    constexpr int kUnroll = 4;
     const int lane = threadIdx.x & 31;
     const unsigned vmask = __ballot_sync(kFull, valid);
     if (vmask == 0u) return true;
@@ -104,38 +103,32 @@ __device__ __forceinline__ bool sweep_staged(const float4 *__restrict__ st,
         const uint32_t L = __shfl_sync(kFull, slen, sg);
         for (uint32_t q = lane; q < L; q += 32) cp_async16(&w.rows[o + q], st + b + q);
     }
-    // this lane's runs, as offsets into the staged rows
+    // this lane's runs, as offsets into the staged rows (an empty run points
+    // at the lane's own row, which the j != i test rejects)
     const float4 me = valid ? me_in : make_float4(1e30f, 1e30f, 1e30f, 1.f);
-    int nr = 0, total = 0;
-    uint32_t self = 0;
     const int plane = g.dims[0] * g.dims[1];
+    uint32_t self = 0;
+    {
+        const uint32_t b4 = __shfl_sync(kFull, sbeg, myrow * 9 + 4);
+        const uint32_t o4 = __shfl_sync(kFull, soff, myrow * 9 + 4);
+        if (valid) self = o4 + (i - b4);
+    }
 #pragma unroll
     for (int r = 0; r < 9; ++r) {
         const int sg = myrow * 9 + r;
         const uint32_t b = __shfl_sync(kFull, sbeg, sg), o = __shfl_sync(kFull, soff, sg);
+        uint32_t packed = self | (self << 16);
         if (valid) {
             const uint32_t kb = (uint32_t)((int)key + (r / 3 - 1) * plane + (r % 3 - 1) * (int)dx);
             const uint32_t rb = __ldg(start + kb - 1), re = __ldg(start + kb + 2);
-            if (r == 4) self = o + (i - b);
-            if (re > rb) {
-                w.runs[nr][lane] = (o + (rb - b)) | ((o + (re - b)) << 16);
-                ++nr;
-                total += (int)(re - rb);
-            }
+            if (re > rb) packed = (o + (rb - b)) | ((o + (re - b)) << 16);
         }
+        w.runs[r][lane] = packed;
     }
     cp_async_wait_all();
     __syncwarp();
     const float rim = 0.5f * me.w + m2;
-    const int tmax = (int)__reduce_max_sync(kFull, (unsigned)total);
-    int cnt = 0, r = 0;
-    uint32_t j = self, jend = self + 1;
-    if (nr > 0) {
-        const uint32_t c = w.runs[0][lane];
-        j = c & 0xffffu;
-        jend = c >> 16;
-    }
-    float4 q = w.rows[j];
+    int cnt = 0;
     auto flush = [&]() {
         const int m = (int)__reduce_max_sync(kFull, (unsigned)cnt);
         for (int kk = 0; kk < m; ++kk) {
@@ -143,33 +136,28 @@ __device__ __forceinline__ bool sweep_staged(const float4 *__restrict__ st,
         }
         cnt = 0;
     };
-    for (int t = 0; t < tmax; t += kUnroll) {
+#pragma unroll 1
+    for (int r = 0; r < 9; ++r) {
+        const uint32_t c = w.runs[r][lane];
+        const uint32_t b = c & 0xffffu;
+        const int len = (int)(c >> 16) - (int)b;
+        const int last = max(len - 1, 0);
+        const int lmax = (int)__reduce_max_sync(kFull, (unsigned)len);
+        for (int t = 0; t < lmax; t += kSweepUnroll) {
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const float4 cur = q;
-            const uint32_t jc = j;
-            ++j;
-            if (j == jend) {
-                ++r;
-                if (r < nr) {
-                    const uint32_t c = w.runs[r][lane];
-                    j = c & 0xffffu;
-                    jend = c >> 16;
-                } else {
-                    j = self;
-                    jend = self + 1;
+            for (int u = 0; u < kSweepUnroll; ++u) {
+                const uint32_t jc = b + (uint32_t)min(t + u, last);
+                const float4 cur = w.rows[jc];
+                const float ddx = me.x - cur.x, ddy = me.y - cur.y, ddz = me.z - cur.z;
+                const float d2 = fmaf(ddz, ddz, fmaf(ddy, ddy, ddx * ddx));
+                const float s = fmaf(0.5f, cur.w, rim);
+                if ((t + u < len) & (jc != self) & (d2 < s * s * kFilter)) {
+                    w.lst[cnt][lane] = (uint16_t)jc;
+                    ++cnt;
                 }
             }
-            q = w.rows[j];
-            const float ddx = me.x - cur.x, ddy = me.y - cur.y, ddz = me.z - cur.z;
-            const float d2 = fmaf(ddz, ddz, fmaf(ddy, ddy, ddx * ddx));
-            const float s = fmaf(0.5f, cur.w, rim);
-            if (d2 < s * s * kFilter && jc != self) {
-                w.lst[cnt][lane] = (uint16_t)jc;
-                ++cnt;
-            }
+            if (__any_sync(kFull, cnt > kStageList - kSweepUnroll)) flush();
         }
-        if (__any_sync(kFull, cnt > kStageList - kUnroll)) flush();
     }
     flush();
     __syncwarp();
