@@ -80,7 +80,9 @@ typedef struct {
 } ug_params;
 
 /* Geometry of one simulation's uniform grid (Sec. IV-A), written on the device.
- *   edge   = largest diameter + 2 * contact_margin
+ *   edge   = S + 8 ulp(C), S = largest diameter + 2 * contact_margin (the largest
+ *            contact distance), C = max(S, largest |coordinate|); the 8 ulps keep
+ *            every contact pair in adjacent boxes despite float32 rounding
  *   origin = (min corner of the agent centres) - edge, per axis
  *   box of an agent b = max(floor((p - origin) / edge), 1) per axis, in IEEE
  *   float32 round-to-nearest arithmetic; dims = box of the max corner + 2, so

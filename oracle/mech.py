@@ -32,7 +32,11 @@ Simulations", Sec. III, Eq. 1 and the paragraph after it; Sec. IV-A for the grid
   Grid (Sec. IV-A, Fig. 4): the box an agent falls in is computed in FP32 on
   purpose, because floating point decides an integer there and the library
   decides it in FP32 too:
-      e = max_i diameter_i + 2m;  o = min_i p_i - e  (per axis);
+      S = max_i diameter_i + 2m (the largest contact distance);
+      e = S + 8 ulp(C), C = max(S, largest |coordinate|): rounding the box
+          coordinate moves an agent by at most ~3 such ulps, so every contact
+          pair stays within adjacent boxes, which is what Sec. IV-A relies on;
+      o = min_i p_i - e  (per axis);
       b = max(floor((p - o) / e), 1);  dims = max(floor((max_i p_i - o) / e), 1) + 2;
       key = (b_z * dims_y + b_y) * dims_x + b_x;  boxes listed in key order,
       agents within a box in input order (stable).
@@ -79,9 +83,11 @@ def grid(state32: np.ndarray, contact_margin: float = 0.0) -> dict:
     st = np.ascontiguousarray(state32, dtype=F32)
     p = st[:, :3]
     m2 = F32(2.0) * F32(contact_margin)
-    e = F32(st[:, 3].max()) + m2
+    S = F32(st[:, 3].max()) + m2                  # largest contact distance
     lo = p.min(axis=0)
     hi = p.max(axis=0)
+    C = max(S, np.abs(lo).max(), np.abs(hi).max())
+    e = F32(S + F32(8.0) * (np.nextafter(C, F32(np.inf)) - C))
     o = (lo - e).astype(F32)
     b = np.floor((p - o) / e).astype(np.int64)
     b = np.maximum(b, 1)

@@ -55,20 +55,29 @@ k_key(const float4 *__restrict__ st, SimArgs sa, const ug_grid_info *__restrict_
     const bool valid = i < sa.n;
     bool uniform;
     const uint32_t sim = cta_sim(sa, first, i, uniform);
-    const unsigned act = __ballot_sync(kFull, valid);
-    if (!valid) return;
-    const ug_grid_info g = geo[sim];
-    int bx, by, bz;
-    const uint32_t k = box_key(__ldg(st + i), g, bx, by, bz);
-    // rows of this warp with the same key share one atomic
-    const unsigned peers = __match_any_sync(act, k);
+    uint32_t k = 0xffffffffu;
+    if (valid) {
+        const ug_grid_info g = geo[sim];
+        int bx, by, bz;
+        k = box_key(__ldg(st + i), g, bx, by, bz);
+    }
+    // rows arrive nearly sorted by box (the previous step's order), so equal
+    // keys mostly sit on consecutive lanes: each run of equal keys takes one
+    // atomic, and its lanes get consecutive provisional ranks
     const int lane = threadIdx.x & 31;
-    const int leader = __ffs(peers) - 1;
+    const uint32_t prevk = __shfl_up_sync(kFull, k, 1);
+    const bool head = lane == 0 || prevk != k;
+    const unsigned heads = __ballot_sync(kFull, head);
+    const int myhead = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+    const unsigned after = lane == 31 ? 0u : heads & (0xffffffffu << (lane + 1));
+    const int nexthead = after ? __ffs(after) - 1 : 32;
     uint32_t base = 0;
-    if (lane == leader) base = atomicAdd(&counts[k], (uint32_t)__popc(peers));
-    base = __shfl_sync(peers, base, leader);
-    rank[i] = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
-    key[i] = k;
+    if (head && valid) base = atomicAdd(&counts[k], (uint32_t)(nexthead - lane));
+    base = __shfl_sync(kFull, base, myhead);
+    if (valid) {
+        rank[i] = base + (uint32_t)(lane - myhead);
+        key[i] = k;
+    }
 }
 
 // ------------------------------------------------------------------ look-back scan
@@ -126,10 +135,11 @@ k_scan(uint32_t *__restrict__ counts, uint32_t *__restrict__ start, Ctrl *ctrl,
         const uint32_t base = t * kScanTile + threadIdx.x * kScanItems;
         uint32_t v[kScanItems];
         if (base + kScanItems <= B) {
-            const uint4 a = *reinterpret_cast<const uint4 *>(counts + base);
-            const uint4 b = *reinterpret_cast<const uint4 *>(counts + base + 4);
-            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+#pragma unroll
+            for (int q = 0; q < kScanItems / 4; ++q) {
+                const uint4 a = *reinterpret_cast<const uint4 *>(counts + base + 4 * q);
+                v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
+            }
         } else {
 #pragma unroll
             for (int k = 0; k < kScanItems; ++k) v[k] = base + k < B ? counts[base + k] : 0u;
@@ -167,13 +177,16 @@ k_scan(uint32_t *__restrict__ counts, uint32_t *__restrict__ start, Ctrl *ctrl,
         __syncthreads();
         uint32_t run = s_prefix + wbase + inc - tsum;
         if (base + kScanItems <= B) {
-            uint4 a, b;
-            a.x = run; run += v[0]; a.y = run; run += v[1]; a.z = run; run += v[2]; a.w = run; run += v[3];
-            b.x = run; run += v[4]; b.y = run; run += v[5]; b.z = run; run += v[6]; b.w = run; run += v[7];
-            *reinterpret_cast<uint4 *>(start + base) = a;
-            *reinterpret_cast<uint4 *>(start + base + 4) = b;
-            *reinterpret_cast<uint4 *>(counts + base) = make_uint4(0u, 0u, 0u, 0u);
-            *reinterpret_cast<uint4 *>(counts + base + 4) = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+            for (int q = 0; q < kScanItems / 4; ++q) {
+                uint4 a;
+                a.x = run; run += v[4 * q];
+                a.y = run; run += v[4 * q + 1];
+                a.z = run; run += v[4 * q + 2];
+                a.w = run; run += v[4 * q + 3];
+                *reinterpret_cast<uint4 *>(start + base + 4 * q) = a;
+                *reinterpret_cast<uint4 *>(counts + base + 4 * q) = make_uint4(0u, 0u, 0u, 0u);
+            }
         } else {
 #pragma unroll
             for (int k = 0; k < kScanItems; ++k) {
@@ -238,7 +251,7 @@ void launch_key(const float4 *st, const SimArgs &sa, const Workspace &w, const u
 void launch_scan(const Workspace &w, uint32_t *start, uint32_t max_boxes, int32_t *status,
                  cudaStream_t s) {
     (void)max_boxes;
-    const unsigned grid = (unsigned)min((int)w.ntiles, 4 * device_sm_count());
+    const unsigned grid = (unsigned)min((int)w.ntiles, 2 * device_sm_count());
     k_scan<<<grid > 0 ? grid : 1, kScanThreads, 0, s>>>(w.counts, start, w.ctrl, w.scan_status,
                                                          status);
 }

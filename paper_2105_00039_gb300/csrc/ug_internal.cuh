@@ -11,8 +11,8 @@
 namespace ug {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kScanThreads = 256;
-constexpr int kScanItems = 8;
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;   // boxes per look-back tile
 constexpr int kBoundsWords = 8;                         // per simulation, see bounds_*()
 constexpr int kBoundsCopiesSingle = 32;                 // spread atomics when nsims == 1
@@ -399,9 +399,18 @@ __device__ __forceinline__ void finalize_grid(const SimArgs &sa, uint32_t *bound
                 }
                 const ug_params P = sim_params(sa, s);
                 const float m2 = 2.0f * P.contact_margin;
-                const float e = __fadd_rn(ord_dec(w[6]), m2);
+                // edge = largest contact distance + 8 ulp of the largest
+                // coordinate magnitude: float32 rounding of a box coordinate
+                // moves an agent by at most ~3 such ulps, so no contact pair
+                // (distance < largest contact distance) can end up two boxes apart
+                const float S = __fadd_rn(ord_dec(w[6]), m2);
+                float C = S;
+                for (int a = 0; a < 3; ++a)
+                    C = fmaxf(C, fmaxf(fabsf(ord_dec(w[a])), fabsf(ord_dec(w[3 + a]))));
+                const float ulpC = __fsub_rn(__uint_as_float(__float_as_uint(C) + 1u), C);
+                const float e = __fadd_rn(S, 8.0f * ulpC);
                 const float mind = -ord_dec(w[7]);
-                bool bad = !(e > 0.0f) || !isfinite(e) || !(mind > 0.0f);
+                bool bad = !(e > 0.0f) || !isfinite(e) || !isfinite(C) || !(mind > 0.0f);
                 g.edge = e;
                 for (int a = 0; a < 3; ++a) {
                     const float lo = -ord_dec(w[a]);

@@ -206,7 +206,9 @@ def test_pair_count_small_lattice():
 def test_grid_hand_example():
     st = np.array([[0, 0, 0, 10], [25, 0, 0, 10]], dtype=np.float32)
     g = O.grid(st)
-    assert g["edge"] == 10 and np.array_equal(g["origin"], [-10, -10, -10])
+    # S = 10, C = 25: ulp(25) = 2^-19, edge = 10 + 8 * 2^-19 = 10 + 2^-16
+    e = 10.0 + 2.0 ** -16
+    assert g["edge"] == np.float32(e) and np.array_equal(g["origin"], np.float32([-e, -e, -e]))
     assert list(g["dims"]) == [5, 3, 3]
     assert list(g["key"]) == [21, 23] and g["nboxes"] == 45
     assert g["start"][21] == 0 and g["start"][22] == 1 and g["start"][24] == 2
@@ -217,6 +219,16 @@ def test_grid_completeness(seed):
     assert check_grid_completeness(P.small_uniform(seed))
     assert check_grid_completeness(P.jittered_lattice(4096, 16, 9.0, 1.5, 9.0, 11.0, seed), 1.5)
     assert check_grid_completeness(P.uniform_cube(2000, 40.0, 8.0, 12.0, seed))
+
+
+def test_grid_edge_margin_keeps_face_pairs_adjacent():
+    # two maximal spheres just touching across a box face far from the origin:
+    # the box edge's rounding margin keeps them in adjacent boxes
+    x0 = np.float32(4096.0)
+    st = np.array([[x0, 0, 0, 10], [np.nextafter(x0 + 10, np.float32(0)), 0, 0, 10]], np.float32)
+    g = O.grid(st)
+    assert g["edge"] > 10 and abs(int(g["box"][0, 0]) - int(g["box"][1, 0])) <= 1
+    assert check_grid_completeness(st)
 
 
 def test_grid_negative_and_tiny_extent():
