@@ -217,6 +217,29 @@ __device__ __forceinline__ uint32_t run_row_key(const ug_grid_info &g, int bx, i
     return g.box_base + (uint32_t)(((bz + dz) * g.dims[1] + (by + dy)) * g.dims[0] + bx);
 }
 
+// The float32 pre-filter of one candidate row q against row i, in Blackwell's
+// packed FP32x2 arithmetic: (dx, dy) = q.xy - p_i.xy and (dz, s) =
+// (q.z, q.w) * (1, 1/2) + (-z_i, r_i + 2m) are one instruction each, the
+// squares two more.  True when |p_i - q|^2 < (r_i + r_q + 2m)^2 (1 + 2^-16).
+struct FilterRow {
+    float2 nxy;   // (-x_i, -y_i)
+    float2 zr;    // (-z_i, r_i + 2m)
+};
+__device__ __forceinline__ FilterRow make_filter_row(const float4 &me, float m2) {
+    FilterRow f;
+    f.nxy = make_float2(-me.x, -me.y);
+    f.zr = make_float2(-me.z, 0.5f * me.w + m2);
+    return f;
+}
+__device__ __forceinline__ bool prefilter(const float4 &q, const FilterRow &f) {
+    const float2 dxy = __fadd2_rn(make_float2(q.x, q.y), f.nxy);
+    const float2 dzs = __ffma2_rn(make_float2(q.z, q.w), make_float2(1.0f, 0.5f), f.zr);
+    const float2 sxy = __fmul2_rn(dxy, dxy);
+    const float2 szs = __fmul2_rn(dzs, dzs);
+    const float d2 = sxy.x + sxy.y + szs.x;
+    return d2 < szs.y * kFilter;
+}
+
 // Visit every candidate j != i of the 27 boxes around row i; `fn(j, row_j)` is
 // called for those passing a float32 distance filter whose 2^-16 relative band
 // keeps every true contact (the exact test is fn's job).
@@ -251,7 +274,7 @@ __device__ __forceinline__ void sweep_neighbours(const float4 *__restrict__ st,
     }
     const int row = g.dims[0], plane = g.dims[0] * g.dims[1];
     const uint32_t self = valid ? i : 0u;
-    const float rim = 0.5f * me.w + m2;
+    const FilterRow fr = make_filter_row(me, m2);
     int cnt = 0;
     auto flush = [&]() {
         const int m = (int)__reduce_max_sync(kFull, (unsigned)cnt);
@@ -280,10 +303,7 @@ __device__ __forceinline__ void sweep_neighbours(const float4 *__restrict__ st,
             for (int u = 0; u < kSweepUnroll; ++u) {
                 const uint32_t jc = b + (uint32_t)min(t + u, last);
                 const float4 cur = __ldg(st + jc);
-                const float dx = me.x - cur.x, dy = me.y - cur.y, dz = me.z - cur.z;
-                const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                const float s = fmaf(0.5f, cur.w, rim);
-                if ((t + u < len) & (jc != self) & (d2 < s * s * kFilter)) {
+                if ((t + u < len) & (jc != self) & prefilter(cur, fr)) {
                     w.lst[cnt][lane] = jc;
                     ++cnt;
                 }

@@ -127,7 +127,7 @@ __device__ __forceinline__ bool sweep_staged(const float4 *__restrict__ st,
     }
     cp_async_wait_all();
     __syncwarp();
-    const float rim = 0.5f * me.w + m2;
+    const FilterRow fr = make_filter_row(me, m2);
     int cnt = 0;
     auto flush = [&]() {
         const int m = (int)__reduce_max_sync(kFull, (unsigned)cnt);
@@ -148,10 +148,7 @@ __device__ __forceinline__ bool sweep_staged(const float4 *__restrict__ st,
             for (int u = 0; u < kSweepUnroll; ++u) {
                 const uint32_t jc = b + (uint32_t)min(t + u, last);
                 const float4 cur = w.rows[jc];
-                const float ddx = me.x - cur.x, ddy = me.y - cur.y, ddz = me.z - cur.z;
-                const float d2 = fmaf(ddz, ddz, fmaf(ddy, ddy, ddx * ddx));
-                const float s = fmaf(0.5f, cur.w, rim);
-                if ((t + u < len) & (jc != self) & (d2 < s * s * kFilter)) {
+                if ((t + u < len) & (jc != self) & prefilter(cur, fr)) {
                     w.lst[cnt][lane] = (uint16_t)jc;
                     ++cnt;
                 }
