@@ -97,7 +97,10 @@ int run_steps(float4 *state, uint32_t *perm, const SimArgs &sa, int nsteps, uint
         o.geo_next = w.geo;
         o.ctrl = w.ctrl;
         o.max_boxes = max_boxes;
-        launch_sweep(kSweepStep, sorted, start, w.geo, sa, o, sweep_block, status, s, w.rank);
+        if (sa.nsims == 1)
+            launch_sweep2(kSweepStep, sorted, start, w.geo, sa, o, status, s, w.rank);
+        else
+            launch_sweep(kSweepStep, sorted, start, w.geo, sa, o, sweep_block, status, s, w.rank);
         std::swap(pcur, pnext);
     }
     mark(1 + 5 * nsteps);
@@ -195,8 +198,8 @@ int ug_compute_forces(const float *state_sorted, const uint32_t *box_start, cons
     sa.bounds_copies = 1;
     SweepOut o{};
     o.force = reinterpret_cast<float4 *>(force);
-    launch_sweep(kSweepForce, reinterpret_cast<const float4 *>(state_sorted), box_start, info, sa, o,
-                 128, status, static_cast<cudaStream_t>(stream));
+    launch_sweep2(kSweepForce, reinterpret_cast<const float4 *>(state_sorted), box_start, info, sa,
+                  o, status, static_cast<cudaStream_t>(stream), nullptr);
     return last_launch();
 }
 

@@ -356,14 +356,12 @@ __device__ __forceinline__ bool row_ok(const float4 &p) {
     return isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && isfinite(p.w) && p.w > 0.0f;
 }
 
-// Accumulate the bounds of one row per thread; every thread of the CTA calls it.
-__device__ __forceinline__ void accumulate_bounds(const SimArgs &sa, const float4 &p, bool valid,
-                                                  uint32_t sim, bool uniform, uint32_t *bounds,
-                                                  int32_t *status) {
+// Accumulate per-thread bounds codes (see bounds_codes; 0 = nothing); every
+// thread of the CTA calls it.
+__device__ __forceinline__ void accumulate_bounds_codes(const SimArgs &sa, uint32_t v[8],
+                                                        bool valid, uint32_t sim, bool uniform,
+                                                        uint32_t *bounds) {
     __shared__ uint32_t s_red[32][kBoundsWords];
-    if (valid && !row_ok(p)) set_status(status, UG_EBADSTATE);
-    uint32_t v[8];
-    bounds_codes(p, valid, v);
     const uint32_t copy = sa.bounds_copies > 1 ? blockIdx.x % sa.bounds_copies : 0u;
     if (uniform) {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -385,6 +383,16 @@ __device__ __forceinline__ void accumulate_bounds(const SimArgs &sa, const float
         for (int k = 0; k < 8; ++k)
             atomicMax(&bounds[((size_t)copy * sa.nsims + sim) * kBoundsWords + k], v[k]);
     }
+}
+
+// Accumulate the bounds of one row per thread; every thread of the CTA calls it.
+__device__ __forceinline__ void accumulate_bounds(const SimArgs &sa, const float4 &p, bool valid,
+                                                  uint32_t sim, bool uniform, uint32_t *bounds,
+                                                  int32_t *status) {
+    if (valid && !row_ok(p)) set_status(status, UG_EBADSTATE);
+    uint32_t v[8];
+    bounds_codes(p, valid, v);
+    accumulate_bounds_codes(sa, v, valid, sim, uniform, bounds);
 }
 
 // Run by the last CTA to finish: turn the bounds into each simulation's grid,
@@ -539,6 +547,10 @@ struct SweepOut {
 void launch_sweep(int mode, const float4 *sorted, const uint32_t *start, const ug_grid_info *geo,
                   const SimArgs &sa, const SweepOut &out, int block, int32_t *status,
                   cudaStream_t s, const uint32_t *skey = nullptr);
+// Two agents per lane (ug_sweep2.cu); single simulation, force or step mode.
+void launch_sweep2(int mode, const float4 *sorted, const uint32_t *start, const ug_grid_info *geo,
+                   const SimArgs &sa, const SweepOut &out, int32_t *status, cudaStream_t s,
+                   const uint32_t *skey);
 void launch_apply(const float4 *st_in, const float4 *force, uint32_t n, const ug_params &p,
                   float4 *st_out, float4 *disp_out, int32_t *status, cudaStream_t s);
 
