@@ -149,6 +149,19 @@ struct ContactGeo {
     float rb;      // radius of b
     float rsum;    // ra + rb (rounded)
 };
+// Eq. 1 for one contact: the force on a from b is coef * (p_a - p_b) with
+// coef = (kappa delta - gamma sqrt(R delta)) / d.  Returns coef; *root_out gets
+// sqrt(R delta).  Explicit roundings keep it bit-identical across kernels.
+__device__ __forceinline__ float eq1_coef(float ra, float rb, float rsum, float delta, float invd,
+                                          float k, float gamma, float *root_out = nullptr) {
+    const float R = __fdividef(__fmul_rn(ra, rb), rsum);
+    const float rd = __fmul_rn(R, delta);
+    const float root = __fmul_rn(rd, rsqrtf(rd));
+    if (root_out) *root_out = root;
+    const float phi = __fmaf_rn(k, delta, -__fmul_rn(gamma, root));
+    return __fmul_rn(phi, invd);
+}
+
 // EXACT_DIFF = false assumes p_a - p_b is exact in float32, which holds by
 // Sterbenz's lemma when |coordinate of a| >= 3 e on every axis and |p_a - p_b|
 // is below the box edge e (see far_from_origin); the residual terms are then 0.
@@ -172,8 +185,11 @@ __device__ __forceinline__ bool contact_t(const float4 &a, float ra, const float
     float s1, e1, D, e2;
     two_sum(px, py, s1, e1);
     two_sum(s1, pz, D, e2);
-    float E = ex + ey + ez + e1 + e2;
-    if (EXACT_DIFF) E += 2.0f * (c.hx * lx + c.hy * ly + c.hz * lz);
+    // every rounding below is spelled out (no compiler FMA contraction), so the
+    // result is the same bits in every kernel that inlines this
+    float E = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(ex, ey), ez), e1), e2);
+    if (EXACT_DIFF)
+        E = __fmaf_rn(2.0f, __fmaf_rn(c.hx, lx, __fmaf_rn(c.hy, ly, __fmul_rn(c.hz, lz))), E);
     c.rb = 0.5f * b.w;
     float sh, sl;
     two_sum(ra, c.rb, sh, sl);
@@ -182,16 +198,16 @@ __device__ __forceinline__ bool contact_t(const float4 &a, float ra, const float
         float t, te;
         two_sum(sh, m2, t, te);
         sh = t;
-        sl = sl + te;
+        sl = __fadd_rn(sl, te);
     }
     float S2, S2e;
     two_prod(sh, sh, S2, S2e);
-    S2e = fmaf(2.0f * sh, sl, S2e);
-    const float q = __fsub_rn(S2, D) + (S2e - E);
+    S2e = __fmaf_rn(__fmul_rn(2.0f, sh), sl, S2e);
+    const float q = __fadd_rn(__fsub_rn(S2, D), __fsub_rn(S2e, E));
     if (!(q > 0.0f) || !(D > 0.0f)) return false;
     c.invd = rsqrtf(D);
-    const float d = D * c.invd;
-    c.delta = __fdividef(q, sh + d);
+    const float d = __fmul_rn(D, c.invd);
+    c.delta = __fdividef(q, __fadd_rn(sh, d));
     return true;
 }
 __device__ __forceinline__ bool contact(const float4 &a, float ra, const float4 &b, float m2,
@@ -320,17 +336,18 @@ __device__ __forceinline__ void sweep_neighbours(const float4 *__restrict__ st,
 __device__ __forceinline__ float3 displacement(float Fx, float Fy, float Fz, float diam,
                                                const ug_params &P, bool *moving_out = nullptr,
                                                bool *capped_out = nullptr) {
-    const float Fn = sqrtf(Fx * Fx + Fy * Fy + Fz * Fz);
+    const float Fn = __fsqrt_rn(__fmaf_rn(Fx, Fx, __fmaf_rn(Fy, Fy, __fmul_rn(Fz, Fz))));
     float3 u = make_float3(0.f, 0.f, 0.f);
     bool moving = Fn > P.adherence, capped = false;
     if (moving) {
-        const float m = P.density * (float)(M_PI / 6.0) * diam * diam * diam;
-        const float c = P.dt / m;
-        u = make_float3(c * Fx, c * Fy, c * Fz);
-        const float vn = sqrtf(u.x * u.x + u.y * u.y + u.z * u.z);
+        const float m = __fmul_rn(__fmul_rn(__fmul_rn(__fmul_rn(P.density, (float)(M_PI / 6.0)),
+                                                      diam), diam), diam);
+        const float c = __fdiv_rn(P.dt, m);
+        u = make_float3(__fmul_rn(c, Fx), __fmul_rn(c, Fy), __fmul_rn(c, Fz));
+        const float vn = __fsqrt_rn(__fmaf_rn(u.x, u.x, __fmaf_rn(u.y, u.y, __fmul_rn(u.z, u.z))));
         if (vn > P.max_disp) {
-            const float s = P.max_disp / vn;
-            u = make_float3(u.x * s, u.y * s, u.z * s);
+            const float s = __fdiv_rn(P.max_disp, vn);
+            u = make_float3(__fmul_rn(u.x, s), __fmul_rn(u.y, s), __fmul_rn(u.z, s));
             capped = true;
         }
     }

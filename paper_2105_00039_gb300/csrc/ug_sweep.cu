@@ -191,14 +191,10 @@ k_sweep(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
                                      : contact_t<true>(me, ri, q, m2, c);
         if (!hit) return false;
         if (MODE != kSweepPairs) {
-            const float R = __fdividef(ri * c.rb, c.rsum);
-            const float rd = R * c.delta;
-            const float root = rd * rsqrtf(rd);
-            const float phi = P.k * c.delta - P.gamma * root;
-            const float coef = phi * c.invd;
-            comp_add(sx, cx, coef * c.hx);
-            comp_add(sy, cy, coef * c.hy);
-            comp_add(sz, cz, coef * c.hz);
+            const float coef = eq1_coef(ri, c.rb, c.rsum, c.delta, c.invd, P.k, P.gamma);
+            comp_add(sx, cx, __fmul_rn(coef, c.hx));
+            comp_add(sy, cy, __fmul_rn(coef, c.hy));
+            comp_add(sz, cz, __fmul_rn(coef, c.hz));
         }
         ++np;
         return true;

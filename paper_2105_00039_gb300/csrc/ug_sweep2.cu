@@ -33,14 +33,10 @@ __device__ __forceinline__ void add_contact(const float4 &me, const float4 &q, f
     const bool hit = exact_diffs ? contact_t<false>(me, ri, q, m2, c)
                                  : contact_t<true>(me, ri, q, m2, c);
     if (!hit) return;
-    const float R = __fdividef(ri * c.rb, c.rsum);
-    const float rd = R * c.delta;
-    const float root = rd * rsqrtf(rd);
-    const float phi = P.k * c.delta - P.gamma * root;
-    const float coef = phi * c.invd;
-    comp_add(a.sx, a.cx, coef * c.hx);
-    comp_add(a.sy, a.cy, coef * c.hy);
-    comp_add(a.sz, a.cz, coef * c.hz);
+    const float coef = eq1_coef(ri, c.rb, c.rsum, c.delta, c.invd, P.k, P.gamma);
+    comp_add(a.sx, a.cx, __fmul_rn(coef, c.hx));
+    comp_add(a.sy, a.cy, __fmul_rn(coef, c.hy));
+    comp_add(a.sz, a.cz, __fmul_rn(coef, c.hz));
     ++a.np;
 }
 
