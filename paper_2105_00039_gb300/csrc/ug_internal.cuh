@@ -418,30 +418,40 @@ __device__ __forceinline__ void finalize_grid(const SimArgs &sa, uint32_t *bound
                                               ug_grid_info *geo, Ctrl *ctrl, uint32_t max_boxes,
                                               int32_t *status) {
     __shared__ unsigned long long s_scan[256];   // blockDim.x <= 256 for every caller
+    constexpr uint32_t kChunk = 64;              // simulations finalised per pass
+    __shared__ uint32_t s_w[kChunk][kBoundsWords];
     __shared__ unsigned long long s_carry;
     __shared__ int s_bad;
     const int tid = threadIdx.x, nt = blockDim.x;
+    const uint32_t copies = sa.bounds_copies;
     if (tid == 0) { s_carry = 0; s_bad = 0; }
     __syncthreads();
-    for (uint32_t c0 = 0; c0 < sa.nsims; c0 += nt) {
+    for (uint32_t c0 = 0; c0 < sa.nsims; c0 += kChunk) {
+        const uint32_t nchunk = min(kChunk, sa.nsims - c0);
+        // max over the copies of every word of this chunk, all threads at once,
+        // resetting the accumulators for the next use
+        for (uint32_t q = tid; q < nchunk * kBoundsWords; q += nt) s_w[q / kBoundsWords][q % kBoundsWords] = 0u;
+        __syncthreads();
+        const uint32_t total_words = copies * nchunk * kBoundsWords;
+        for (uint32_t q = tid; q < total_words; q += nt) {
+            const uint32_t cp = q / (nchunk * kBoundsWords);
+            const uint32_t rem = q - cp * nchunk * kBoundsWords;
+            uint32_t *slot = &bounds[((size_t)cp * sa.nsims + c0) * kBoundsWords + rem];
+            const uint32_t v = *(volatile uint32_t *)slot;
+            *slot = 0u;
+            if (v) atomicMax(&s_w[rem / kBoundsWords][rem % kBoundsWords], v);
+        }
+        __syncthreads();
         const uint32_t s = c0 + tid;
         unsigned long long nb = 0;
         ug_grid_info g{};
-        if (s < sa.nsims) {
+        if (tid < (int)nchunk) {
             const uint32_t a0 = sim_begin(sa, s), a1 = sim_end(sa, s);
             g.agent_base = a0;
             g.nagents = a1 - a0;
             if (a1 > a0) {
                 uint32_t w[8];
-                for (int k = 0; k < 8; ++k) {
-                    uint32_t m = 0;
-                    for (uint32_t cp = 0; cp < sa.bounds_copies; ++cp) {
-                        uint32_t *slot = &bounds[((size_t)cp * sa.nsims + s) * kBoundsWords + k];
-                        m = max(m, *(volatile uint32_t *)slot);
-                        *slot = 0u;
-                    }
-                    w[k] = m;
-                }
+                for (int k = 0; k < 8; ++k) w[k] = s_w[tid][k];
                 const ug_params P = sim_params(sa, s);
                 const float m2 = 2.0f * P.contact_margin;
                 // edge = largest contact distance + 8 ulp of the largest
@@ -481,7 +491,7 @@ __device__ __forceinline__ void finalize_grid(const SimArgs &sa, uint32_t *bound
         }
         const unsigned long long incl = s_scan[tid];
         const unsigned long long base = s_carry + incl - nb;
-        if (s < sa.nsims) {
+        if (tid < (int)nchunk) {
             g.box_base = (uint32_t)min(base, 0xffffffffull);
             g.nboxes = (uint32_t)nb;
             geo[s] = g;
