@@ -209,20 +209,29 @@ def run_ours(args, world, rank, local, pg):
         pg.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        # the metric: K plain bench steps (kernels chained with programmatic
+        # dependent launch), each preceded by an L2 flush outside its events
         wall0 = time.perf_counter()
         for k in range(args.steps):
             flush.zero_()
             starts[k].record(stream)
             reset()
-            sp.step_traced(x, perm, prm, SIM_STEPS, events)
+            sp.step(x, perm, prm, SIM_STEPS)
             ends[k].record(stream)
-            ends[k].synchronize()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        # per-kernel durations: the same K bench steps again with CUDA events
+        # recorded between the kernels (which also un-chains them)
+        for k in range(args.steps):
+            flush.zero_()
+            reset()
+            sp.step_traced(x, perm, prm, SIM_STEPS, events)
+            events[-1].synchronize()
             kern_ms["bounds"] += events[0].elapsed_time(events[1])
             for t in range(SIM_STEPS):
                 for j, nm in enumerate(names):
                     kern_ms[nm] += events[1 + 5 * t + j].elapsed_time(events[2 + 5 * t + j])
         torch.cuda.synchronize()
-        wall = time.perf_counter() - wall0
     if pg is not None:
         pg.barrier()
     sp.check("timed steps")
@@ -262,6 +271,7 @@ def run_ours(args, world, rank, local, pg):
                      "step_alg_gbs": step_gbs, "step_frac": step_gbs / hbm},
         "kernel_ms_share": {k: v / sum(kern_ms.values()) for k, v in kern_ms.items()},
         "gpu_launches": args.steps * (2 + 5 * SIM_STEPS),
+        "kernel_ms_per_step_traced": {k: v / (args.steps * SIM_STEPS) for k, v in kern_ms.items()},
         "clocks": clk.summary(),
         "wall_s_timed_region": wall,
     }

@@ -25,6 +25,7 @@ namespace ug {
 __global__ void __launch_bounds__(256)
 k_bounds(const float4 *__restrict__ st, SimArgs sa, uint32_t *bounds, ug_grid_info *geo,
          Ctrl *ctrl, uint32_t max_boxes, int32_t *status) {
+    chain_begin();
     if (cta_failed(status)) return;
     const uint32_t first = blockIdx.x * blockDim.x;
     const uint32_t i = first + threadIdx.x;
@@ -42,6 +43,7 @@ k_key(const float4 *__restrict__ st, SimArgs sa, const ug_grid_info *__restrict_
       Ctrl *ctrl, uint32_t *counts, uint32_t *__restrict__ key, uint32_t *__restrict__ rank,
       unsigned long long *scan_status, uint32_t ntiles, ug_grid_info *geo_save,
       int32_t *status) {
+    chain_begin();
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t t = gtid; t < ntiles; t += stride) scan_status[t] = 0ull;
@@ -123,6 +125,7 @@ k_scan(uint32_t *__restrict__ counts, uint32_t *__restrict__ start, Ctrl *ctrl,
        unsigned long long *tstat, int32_t *status) {
     __shared__ uint32_t s_tile, s_prefix;
     __shared__ uint32_t s_warp[kScanThreads / 32];
+    chain_begin();
     if (cta_failed(status)) return;
     const uint32_t B = *(volatile uint32_t *)&ctrl->total_boxes;
     const uint32_t ntiles = (B + kScanTile - 1) / kScanTile;
@@ -207,6 +210,7 @@ __global__ void __launch_bounds__(256)
 k_place(const uint32_t *__restrict__ key, const uint32_t *__restrict__ rank,
         const uint32_t *__restrict__ start, uint32_t *__restrict__ tmp, uint32_t n,
         int32_t *status) {
+    chain_begin();
     if (cta_failed(status)) return;
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) tmp[__ldg(start + __ldg(key + i)) + __ldg(rank + i)] = i;
@@ -218,6 +222,7 @@ k_canon(const uint32_t *__restrict__ tmp, const uint32_t *__restrict__ key,
         const uint32_t *__restrict__ perm_in, float4 *__restrict__ st_out,
         uint32_t *__restrict__ perm_out, uint32_t *__restrict__ sigma, uint32_t n,
         uint32_t *__restrict__ skey, int32_t *status) {
+    chain_begin();
     if (cta_failed(status)) return;
     const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
@@ -238,34 +243,34 @@ static inline unsigned blocks_for(uint32_t n, int t) { return (unsigned)((n + t 
 
 void launch_bounds(const float4 *st, const SimArgs &sa, const Workspace &w, ug_grid_info *geo,
                    uint32_t max_boxes, int32_t *status, cudaStream_t s) {
-    k_bounds<<<blocks_for(sa.n, 256), 256, 0, s>>>(st, sa, w.bounds, geo, w.ctrl, max_boxes,
-                                                   status);
+    launch_chained(k_bounds, blocks_for(sa.n, 256), 256, s, st, sa, w.bounds, geo, w.ctrl,
+                   max_boxes, status);
 }
 
 void launch_key(const float4 *st, const SimArgs &sa, const Workspace &w, const ug_grid_info *geo,
                 ug_grid_info *geo_save, int32_t *status, cudaStream_t s) {
-    k_key<<<blocks_for(sa.n, 256), 256, 0, s>>>(st, sa, geo, w.ctrl, w.counts, w.key, w.rank,
-                                                w.scan_status, w.ntiles, geo_save, status);
+    launch_chained(k_key, blocks_for(sa.n, 256), 256, s, st, sa, geo, w.ctrl, w.counts, w.key,
+                   w.rank, w.scan_status, w.ntiles, geo_save, status);
 }
 
 void launch_scan(const Workspace &w, uint32_t *start, uint32_t max_boxes, int32_t *status,
                  cudaStream_t s) {
     (void)max_boxes;
     const unsigned grid = (unsigned)min((int)w.ntiles, 2 * device_sm_count());
-    k_scan<<<grid > 0 ? grid : 1, kScanThreads, 0, s>>>(w.counts, start, w.ctrl, w.scan_status,
-                                                         status);
+    launch_chained(k_scan, grid > 0 ? grid : 1u, (unsigned)kScanThreads, s, w.counts, start, w.ctrl,
+                   w.scan_status, status);
 }
 
 void launch_place(const Workspace &w, const uint32_t *start, uint32_t n, int32_t *status,
                   cudaStream_t s) {
-    k_place<<<blocks_for(n, 256), 256, 0, s>>>(w.key, w.rank, start, w.tmp, n, status);
+    launch_chained(k_place, blocks_for(n, 256), 256, s, w.key, w.rank, start, w.tmp, n, status);
 }
 
 void launch_canon(const Workspace &w, const uint32_t *start, const float4 *st_in,
                   const uint32_t *perm_in, float4 *st_sorted, uint32_t *perm_out, uint32_t *sigma,
                   uint32_t n, int32_t *status, cudaStream_t s, uint32_t *skey) {
-    k_canon<<<blocks_for(n, 256), 256, 0, s>>>(w.tmp, w.key, start, st_in, perm_in, st_sorted,
-                                               perm_out, sigma, n, skey, status);
+    launch_chained(k_canon, blocks_for(n, 256), 256, s, w.tmp, w.key, start, st_in, perm_in,
+                   st_sorted, perm_out, sigma, n, skey, status);
 }
 
 }  // namespace ug

@@ -37,6 +37,33 @@ struct SimArgs {
     uint32_t bounds_copies;   // copies of the bounds accumulators (atomic spreading)
 };
 
+// ------------------------------------------------------------------ dependent launch
+// Kernels of one step form a chain on the caller's stream.  Each is launched
+// with programmatic stream serialization (launch_chained): it may be scheduled
+// while its predecessor's last wave still runs, and waits at chain_begin() until
+// the predecessor has completed and its writes are visible.  chain_begin() must
+// be the first thing a chained kernel does.
+__device__ __forceinline__ void chain_begin() {
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_chained(void (*kernel)(KArgs...), unsigned grid, unsigned block,
+                           cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // ------------------------------------------------------------------ status
 __device__ __forceinline__ void set_status(int32_t *status, int32_t code) {
     atomicCAS(status, 0, code);

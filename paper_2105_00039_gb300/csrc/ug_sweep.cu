@@ -167,6 +167,7 @@ k_sweep(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
         const ug_grid_info *__restrict__ geo, const uint32_t *__restrict__ skey, SimArgs sa,
         SweepOut out, int32_t *status) {
     __shared__ WarpSmem wsm[T / 32];
+    chain_begin();
     if (cta_failed(status)) return;
     const uint32_t first = blockIdx.x * T;
     const uint32_t i = first + threadIdx.x;
@@ -257,10 +258,11 @@ static void launch_mode(const float4 *sorted, const uint32_t *start, const ug_gr
                         const SimArgs &sa, const SweepOut &out, int block, int32_t *status,
                         cudaStream_t s, const uint32_t *skey) {
     if (block == 64)
-        k_sweep<MODE, 64><<<(sa.n + 63) / 64, 64, 0, s>>>(sorted, start, geo, skey, sa, out, status);
+        launch_chained(k_sweep<MODE, 64>, (sa.n + 63) / 64, 64u, s, sorted, start, geo, skey, sa,
+                       out, status);
     else
-        k_sweep<MODE, 128><<<(sa.n + 127) / 128, 128, 0, s>>>(sorted, start, geo, skey, sa, out,
-                                                             status);
+        launch_chained(k_sweep<MODE, 128>, (sa.n + 127) / 128, 128u, s, sorted, start, geo, skey,
+                       sa, out, status);
 }
 
 void launch_sweep(int mode, const float4 *sorted, const uint32_t *start, const ug_grid_info *geo,

@@ -41,11 +41,12 @@ __device__ __forceinline__ void add_contact(const float4 &me, const float4 &q, f
 }
 
 template <int MODE, int T>
-__global__ void __launch_bounds__(T)
+__global__ void __launch_bounds__(T, 8)
 k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
          const ug_grid_info *__restrict__ geo, const uint32_t *__restrict__ skey, SimArgs sa,
          SweepOut out, int32_t *status) {
     __shared__ WarpLists2 wl[T / 32];
+    chain_begin();
     if (cta_failed(status)) return;
     const int lane = threadIdx.x & 31;
     WarpLists2 &w = wl[threadIdx.x >> 5];
@@ -164,9 +165,9 @@ void launch_sweep2(int mode, const float4 *sorted, const uint32_t *start, const 
     constexpr int T = 128;
     const unsigned grid = (unsigned)((sa.n + 2 * T - 1) / (2 * T));
     if (mode == kSweepForce)
-        k_sweep2<kSweepForce, T><<<grid, T, 0, s>>>(sorted, start, geo, skey, sa, out, status);
+        launch_chained(k_sweep2<kSweepForce, T>, grid, T, s, sorted, start, geo, skey, sa, out, status);
     else
-        k_sweep2<kSweepStep, T><<<grid, T, 0, s>>>(sorted, start, geo, skey, sa, out, status);
+        launch_chained(k_sweep2<kSweepStep, T>, grid, T, s, sorted, start, geo, skey, sa, out, status);
 }
 
 }  // namespace ug
