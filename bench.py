@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched, adjoint and density-sweep rows")
     return ap.parse_args()
 
 
@@ -300,12 +302,200 @@ def run_ours(args, world, rank, local, pg):
                        "unit": "agent-steps/s", "h2d_bytes_per_step": 16 * n,
                        "d2h_bytes_per_step": 16 * n}
 
+    if not args.no_extras:
+        line["batched"] = measure_batched(dev, flush)
+        line["adjoint"] = measure_adjoint(dev, flush)
+        line["density_sweep"] = measure_density(dev, flush)
+
     if rank == 0 and not args.no_cpu_baseline:
         rate, secs = cpu_oracle_rate(st, 3)
         line["cpu_baseline"] = {"value": rate, "unit": "agent-steps/s", "cores": 1, "kind": "oracle",
                                 "sample": f"3 FP64 oracle steps of all 2^20 cells ({secs:.1f} s)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------- extra rows
+def _timed(fn, reps, flush=None):
+    """Mean milliseconds of fn() over reps runs, CUDA events on the current
+    stream, L2 flushed before each run (outside the events)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    tot = 0.0
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    return tot / reps
+
+
+def measure_batched(dev, flush, nsims=256, nsteps=50, reps=3):
+    """256 independent simulations (agent counts log-uniform in [1e3, 2e5], mean
+    neighbours U[4, 40]), 50 steps: the batched step captured as one CUDA graph
+    versus the 256 simulations run one after another with the plain step."""
+    import torch
+
+    from paper_2105_00039_gb300 import populations as P
+    from paper_2105_00039_gb300 import ugmech as U
+    st, offs = P.batched_population(nsims=nsims, seed=0)
+    n = len(st)
+    x0 = torch.from_numpy(st).to(dev)
+    offs_t = torch.from_numpy(offs.astype(np.int32)).to(dev)
+    prm = U.Params()
+    pdev = torch.stack([prm.as_tensor(dev) for _ in range(nsims)])
+    parts = [x0[int(offs[k]):int(offs[k + 1])] for k in range(nsims)]
+    # generous per-simulation box capacity: dense random clouds expand while relaxing
+    caps = [4 * U.estimate_max_boxes(p, 0.0, slack=1.0, extra_extent=24.0) + 1000 for p in parts]
+    mb = int(sum(caps))
+    sp = U.Stepper(n, mb, dev, nsims=nsims)
+    x = torch.empty_like(x0)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    tune = U.tune_batched(x0, offs_t, pdev, nsims, mb)
+    lib = U.load()
+
+    def reset():
+        x.copy_(x0)
+        U._check(lib.ug_iota(U._ptr(perm), n, U._stream()), "ug_iota")
+
+    def batched():
+        sp.step_batched(x, perm, offs_t, pdev, nsteps, tune)
+
+    s = torch.cuda.Stream(device=dev)
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        reset()
+        batched()                                  # warm-up outside capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            batched()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+
+    def run_graph():
+        reset()
+        g.replay()
+    run_graph()
+    sp.check("batched")
+    t_batched = _timed(run_graph, reps, flush)
+    sp.check("batched")
+    # sequential plain runs, each simulation with its own workspace
+    steppers = [U.Stepper(len(p), caps[k], dev) for k, p in enumerate(parts)]
+    xs = [torch.empty_like(p) for p in parts]
+    ps = [torch.empty(len(p), dtype=torch.int32, device=dev) for p in parts]
+
+    def sequential():
+        for k in range(nsims):
+            xs[k].copy_(parts[k])
+            U._check(lib.ug_iota(U._ptr(ps[k]), len(parts[k]), U._stream()), "ug_iota")
+            steppers[k].step(xs[k], ps[k], prm, nsteps)
+    sequential()
+    torch.cuda.synchronize()
+    t_seq = _timed(sequential, reps, flush)
+    for k in range(0, nsims, 37):
+        steppers[k].check("sequential")
+    same = all(torch.equal(x[int(offs[k]):int(offs[k + 1])], xs[k]) for k in range(nsims))
+    return {"workload": f"{nsims} simulations, {n} agents in total, {nsteps} steps",
+            "batched_graph_ms": t_batched, "sequential_plain_ms": t_seq,
+            "batched_agent_steps_per_s": n * nsteps / (t_batched / 1e3),
+            "sequential_agent_steps_per_s": n * nsteps / (t_seq / 1e3),
+            "speedup": t_seq / t_batched, "bit_identical_to_plain": bool(same),
+            "tuned_sweep_block": int(tune.sweep_block)}
+
+
+def measure_adjoint(dev, flush, side=64, nsteps=50, ckpt=10, reps=3):
+    """Differentiable workload: side^3 lattice cells, 50 steps, checkpoints every
+    10; forward (checkpointed) and backward (ug_step_backward per segment)."""
+    import torch
+
+    from paper_2105_00039_gb300 import populations as P
+    from paper_2105_00039_gb300 import ugmech as U
+    from paper_2105_00039_gb300.autograd import trajectory
+    st = P.lattice_cube(side, seed=5)
+    x0 = torch.from_numpy(st).to(dev)
+    tgt = x0[:, :3] + 0.1
+    prm = U.Params(adherence=0.0)
+    mb = U.estimate_max_boxes(x0, 0.0, slack=2.0)
+    state = {}
+
+    def fwd():
+        x = x0.clone().requires_grad_(True)
+        k = torch.tensor(2.0, requires_grad=True)
+        gm = torch.tensor(1.0, requires_grad=True)
+        out = trajectory(x, k, gm, prm, nsteps, ckpt, mb)
+        state["loss"] = ((out[:, :3] - tgt) ** 2).mean()
+        state["leaves"] = (x, k, gm)
+
+    def bwd():
+        state["loss"].backward()
+
+    fwd(); bwd(); torch.cuda.synchronize()
+    f_ms, b_ms = 0.0, 0.0
+    for _ in range(reps):
+        f_ms += _timed(fwd, 1, flush)
+        b_ms += _timed(bwd, 1, flush)
+    f_ms /= reps
+    b_ms /= reps
+    # the plain forward alone (no checkpoint copies, no autograd) for reference
+    sp = U.Stepper(len(st), mb, dev)
+    x = torch.empty_like(x0)
+    perm = torch.empty(len(st), dtype=torch.int32, device=dev)
+    lib = U.load()
+
+    def plain():
+        x.copy_(x0)
+        U._check(lib.ug_iota(U._ptr(perm), len(st), U._stream()), "ug_iota")
+        sp.step(x, perm, prm, nsteps)
+    plain(); torch.cuda.synchronize()
+    p_ms = _timed(plain, reps, flush)
+    return {"workload": f"{side}^3 = {side ** 3} lattice cells, {nsteps} steps, checkpoint every {ckpt}",
+            "forward_ms": f_ms, "backward_ms": b_ms, "plain_forward_ms": p_ms,
+            "backward_over_forward": b_ms / f_ms, "backward_over_plain_forward": b_ms / p_ms}
+
+
+def measure_density(dev, flush, reps=2, nsteps=20):
+    """Benchmark-B style density sweep: uniform centres in cubes sized for a mean
+    of 2, 8, 32, 64 overlapping neighbours (4,194,304 cells) and 12 (16,777,216
+    cells), max displacement 0 (frozen), 20 steps each."""
+    import torch
+
+    from paper_2105_00039_gb300 import populations as P
+    from paper_2105_00039_gb300 import ugmech as U
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        hbm = float(json.load(f)["hbm_gbs"])
+    prm = U.Params(max_disp=0.0)
+    rows = []
+    lib = U.load()
+    for n, nbar in ((1 << 22, 2), (1 << 22, 8), (1 << 22, 32), (1 << 22, 64), (1 << 24, 12)):
+        st = P.density_cube(n, float(nbar), seed=nbar)
+        x0 = torch.from_numpy(st).to(dev)
+        del st
+        mb = U.estimate_max_boxes(x0, 0.0, slack=1.05)
+        sp = U.Stepper(n, mb, dev)
+        x = torch.empty_like(x0)
+        perm = torch.empty(n, dtype=torch.int32, device=dev)
+
+        def run():
+            x.copy_(x0)
+            U._check(lib.ug_iota(U._ptr(perm), n, U._stream()), "ug_iota")
+            sp.step(x, perm, prm, nsteps)
+        run(); sp.check("density"); torch.cuda.synchronize()
+        ms = _timed(run, reps, flush)
+        sp.check("density")
+        per_step_s = ms / 1e3 / nsteps
+        alg = BYTES_PER_AGENT_STEP * n + BYTES_PER_BOX * mb / 1.05
+        rows.append({"n_agents": n, "mean_neighbours_target": nbar,
+                     "agent_steps_per_s": n * nsteps / (ms / 1e3), "ms_per_step": per_step_s * 1e3,
+                     "step_alg_gbs": alg / per_step_s / 1e9, "step_hbm_frac": alg / per_step_s / 1e9 / hbm})
+        del x0, x, perm, sp
+        torch.cuda.empty_cache()
+    return rows
 
 
 def main():
