@@ -33,6 +33,30 @@ SIM_STEPS = 100
 BYTES_PER_AGENT_SWEEP = 32          # sweep + move: read 16 B row, write 16 B row
 BYTES_PER_AGENT_STEP = 88           # whole step (grid bin 16, scatter 40, sweep 32)
 BYTES_PER_BOX = 12
+# algorithmic FP32 operations: distance pre-test per candidate pair (3 sub,
+# 3 mul/fma, 1 add, 1 mul, 1 compare), Eq. 1 per contact (delta: sqrt + sub; R:
+# mul, add, div; sqrt(R delta): mul + sqrt; phi: 2 mul + sub; direction: div +
+# 3 mul; sum: 3 add) and the displacement per agent (|F|, mass, dt/m, 3 mul,
+# |v|, cap test, 3 add)
+FLOPS_PER_CANDIDATE = 9
+FLOPS_PER_CONTACT = 17
+FLOPS_PER_AGENT = 25
+# FP32 roof: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) of one k_sweep2 launch on this workload, from the
+# ncu capture summarised in profiles/k_sweep2_lattice1m.md (cache flushed)
+SWEEP_DRAM_BYTES = 23.520e6 + 1.024e3
+SWEEP_DRAM_BYTES_SRC = "814c59c07fbeda56"      # sha256[:16] of ug_sweep2.cu + ug_internal.cuh when captured
+
+
+def sweep_traffic():
+    """The captured DRAM bytes if the sweep's source is unchanged since, else None."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("ug_sweep2.cu", "ug_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2105_00039_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return SWEEP_DRAM_BYTES if h.hexdigest()[:16] == SWEEP_DRAM_BYTES_SRC else None
 
 
 def parse():
@@ -137,6 +161,24 @@ def cpu_oracle_rate(state, nsteps_sample: int):
         st = O.step(st, O.Params())["state"]
     dt = time.perf_counter() - t0
     return len(state) * nsteps_sample / dt, dt
+
+
+def candidates_and_contacts(U, x, prm):
+    """Mean candidates (agents in the 27 surrounding boxes, self excluded) and
+    contacts per agent of a population, from the library's grid and forces.
+    Measurement only: the box counts are summed over 3x3x3 neighbourhoods with
+    torch on the box table."""
+    import torch
+    srt, perm, start, info, _ = U.grid_build(x, contact_margin=prm.contact_margin)
+    g = U.grid_info_from_bytes(info)
+    dx, dy, dz = g["dims"]
+    cnt = (start[1:g["nboxes"] + 1] - start[:g["nboxes"]]).to(torch.float64).reshape(dz, dy, dx)
+    nb = torch.nn.functional.conv3d(cnt[None, None], torch.ones(1, 1, 3, 3, 3, dtype=torch.float64,
+                                                                   device=cnt.device), padding=1)[0, 0]
+    n = x.shape[0]
+    cand = float((cnt * nb).sum().item() - n) / n
+    F = U.compute_forces(srt, start, info, prm)
+    return cand, float(F[:, 3].double().mean().item())
 
 
 def run_reference(args, world, rank, pg):
@@ -252,6 +294,12 @@ def run_ours(args, world, rank, local, pg):
     alg_bytes = {"sweep": BYTES_PER_AGENT_SWEEP * n, "canon": 48 * n, "key": 24 * n,
                  "place": 16 * n, "scan": 12 * max_boxes, "bounds": 16 * n}[dom]
     achieved = alg_bytes / (avg_launch_ms / 1000.0) / 1e9
+    # candidates and contacts at the start and the end of a bench step
+    c0, k0 = candidates_and_contacts(U, x0, prm)
+    c1, k1 = candidates_and_contacts(U, x.contiguous(), prm)
+    cand, cont = 0.5 * (c0 + c1), 0.5 * (k0 + k1)
+    alg_flops = n * (FLOPS_PER_CANDIDATE * cand + FLOPS_PER_CONTACT * cont + FLOPS_PER_AGENT)
+    alu_tflops = alg_flops / (avg_launch_ms / 1000.0) / 1e12
     # whole-step HBM roofline (algorithmic bytes of the method per step)
     step_alg = (BYTES_PER_AGENT_STEP * n + BYTES_PER_BOX * max_boxes / 1.5) * SIM_STEPS
     step_gbs = step_alg / (ms_per_step / 1000.0) / 1e9
@@ -266,11 +314,18 @@ def run_ours(args, world, rank, local, pg):
                    "n_agents": n, "sim_steps_per_step": SIM_STEPS, "max_boxes": max_boxes,
                    "l2": "flushed (256 MB write) before each timed step, outside its events",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
-                     "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": alu_tflops,
+                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": alu_tflops / FP32_PEAK_TFLOPS,
+                     "traffic": sweep_traffic() if dom == "sweep" else None,
                      "avg_launch_us": avg_launch_ms * 1000.0,
-                     "alg_bytes_per_launch": alg_bytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
-                     "step_alg_gbs": step_gbs, "step_frac": step_gbs / hbm},
+                     "alg_flops_per_launch": alg_flops,
+                     "candidates_per_agent": cand, "contacts_per_agent": cont,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                     "note": "issue-bound: 65% of issue slots busy (ncu), see profiles/k_sweep2_lattice1m.md",
+                     "hbm": {"achieved_gbs": achieved, "peak_gbs": hbm, "frac": achieved / hbm,
+                             "alg_bytes_per_launch": alg_bytes,
+                             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
+                     "step_alg_gbs": step_gbs, "step_hbm_frac": step_gbs / hbm},
         "kernel_ms_share": {k: v / sum(kern_ms.values()) for k, v in kern_ms.items()},
         "gpu_launches": args.steps * (2 + 5 * SIM_STEPS),
         "kernel_ms_per_step_traced": {k: v / (args.steps * SIM_STEPS) for k, v in kern_ms.items()},
