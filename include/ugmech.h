@@ -100,10 +100,15 @@ typedef struct {
     uint32_t reserved;
 } ug_grid_info; /* 48 bytes */
 
-/* Launch tuning for the batched step (autotuned by ug_tune_batched). */
+/* Launch tuning for the batched step (autotuned by ug_tune_batched).
+ *   agents_per_lane 2: each lane sweeps two box-sorted agents over their merged
+ *                      neighbour runs (sweep_block is then fixed at 128);
+ *                   1: one agent per lane with shared-memory staging, CTAs of
+ *                      sweep_block threads.  0 = default (2). */
 typedef struct {
-    int32_t sweep_block; /* threads per CTA of the force sweep: 64 or 128; 0 = default (128) */
-    int32_t reserved[7];
+    int32_t sweep_block;      /* 64 or 128; 0 = default (128) */
+    int32_t agents_per_lane;  /* 1 or 2; 0 = default (2) */
+    int32_t reserved[6];
 } ug_tuning;
 
 /* ------------------------------------------------------------------ workspace */
@@ -215,9 +220,11 @@ int ug_step_batched(float *state, uint32_t *perm, const uint32_t *sim_offset, ui
                     uint32_t max_boxes, const ug_tuning *tuning, void *ws, size_t ws_bytes,
                     int32_t *status, void *stream);
 
-/* Time the sweep with each candidate block size on the given batched problem
- * (one step each, on scratch copies inside ws) and write the fastest to *best
- * (HOST pointer).  Synchronises the stream. */
+/* Time the sweep with each candidate configuration (one agent per lane with 64
+ * or 128 threads per CTA, two agents per lane) on the given batched problem and
+ * write the fastest to *best (HOST pointer).  Needs ws_bytes >=
+ * ug_workspace_bytes(n_total, nsims, max_boxes) + 16 * n_total + 512.
+ * Synchronises the stream. */
 int ug_tune_batched(const float *state, const uint32_t *sim_offset, uint32_t nsims,
                     uint32_t n_total, const ug_params *params, uint32_t max_boxes,
                     ug_tuning *best, void *ws, size_t ws_bytes, void *stream);

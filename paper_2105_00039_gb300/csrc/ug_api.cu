@@ -64,8 +64,8 @@ static int cuda_status(cudaError_t e) { return e == cudaSuccess ? UG_OK : UG_ECU
 static int last_launch() { return cuda_status(cudaGetLastError()); }
 
 int run_steps(float4 *state, uint32_t *perm, const SimArgs &sa, int nsteps, uint32_t max_boxes,
-              const Workspace &w, int sweep_block, const StepSaves *saves, int32_t *status,
-              cudaStream_t s, cudaEvent_t const *events) {
+              const Workspace &w, int sweep_block, int agents_per_lane, const StepSaves *saves,
+              int32_t *status, cudaStream_t s, cudaEvent_t const *events) {
     const uint32_t n = sa.n;
     auto mark = [&](int k) {
         if (events) cudaEventRecord(events[k], s);
@@ -97,7 +97,7 @@ int run_steps(float4 *state, uint32_t *perm, const SimArgs &sa, int nsteps, uint
         o.geo_next = w.geo;
         o.ctrl = w.ctrl;
         o.max_boxes = max_boxes;
-        if (sa.nsims == 1)
+        if (agents_per_lane == 2)
             launch_sweep2(kSweepStep, sorted, start, w.geo, sa, o, status, s, w.rank);
         else
             launch_sweep(kSweepStep, sorted, start, w.geo, sa, o, sweep_block, status, s, w.rank);
@@ -250,8 +250,8 @@ int ug_step(float *state, uint32_t *perm, uint32_t n, ug_params p, int32_t nstep
     sa.n = n;
     sa.pval = p;
     sa.bounds_copies = bounds_copies(1);
-    return run_steps(reinterpret_cast<float4 *>(state), perm, sa, nsteps, max_boxes, w, 128, nullptr,
-                     status, static_cast<cudaStream_t>(stream));
+    return run_steps(reinterpret_cast<float4 *>(state), perm, sa, nsteps, max_boxes, w, 128, 2,
+                     nullptr, status, static_cast<cudaStream_t>(stream));
 }
 
 int ug_step_traced(float *state, uint32_t *perm, uint32_t n, ug_params p, int32_t nsteps,
@@ -269,8 +269,8 @@ int ug_step_traced(float *state, uint32_t *perm, uint32_t n, ug_params p, int32_
     sa.n = n;
     sa.pval = p;
     sa.bounds_copies = bounds_copies(1);
-    return run_steps(reinterpret_cast<float4 *>(state), perm, sa, nsteps, max_boxes, w, 128, nullptr,
-                     status, static_cast<cudaStream_t>(stream),
+    return run_steps(reinterpret_cast<float4 *>(state), perm, sa, nsteps, max_boxes, w, 128, 2,
+                     nullptr, status, static_cast<cudaStream_t>(stream),
                      reinterpret_cast<cudaEvent_t const *>(events));
 }
 
@@ -291,9 +291,10 @@ int ug_step_batched(float *state, uint32_t *perm, const uint32_t *sim_offset, ui
     sa.nsims = nsims;
     sa.n = n_total;
     sa.bounds_copies = bounds_copies(nsims);
-    int block = tuning && tuning->sweep_block ? tuning->sweep_block : 128;
-    if (block != 64 && block != 128) return UG_EINVAL;
-    return run_steps(reinterpret_cast<float4 *>(state), perm, sa, nsteps, max_boxes, w, block,
+    const int block = tuning && tuning->sweep_block ? tuning->sweep_block : 128;
+    const int apl = tuning && tuning->agents_per_lane ? tuning->agents_per_lane : 2;
+    if ((block != 64 && block != 128) || (apl != 1 && apl != 2)) return UG_EINVAL;
+    return run_steps(reinterpret_cast<float4 *>(state), perm, sa, nsteps, max_boxes, w, block, apl,
                      nullptr, status, static_cast<cudaStream_t>(stream));
 }
 
@@ -303,6 +304,7 @@ int ug_tune_batched(const float *state, const uint32_t *sim_offset, uint32_t nsi
     if (!best) return UG_EINVAL;
     memset(best, 0, sizeof(*best));
     best->sweep_block = 128;
+    best->agents_per_lane = 2;
     if (n_total == 0) return UG_OK;
     if (!rows_ok(state) || !sim_offset || nsims == 0 || !params || !ws || !aligned(ws, 256) ||
         max_boxes < 27)
@@ -332,21 +334,31 @@ int ug_tune_batched(const float *state, const uint32_t *sim_offset, uint32_t nsi
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return UG_ECUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return UG_ECUDA; }
-    const int cands[2] = {64, 128};
+    // candidates: (agents per lane, threads per CTA)
+    const int cands[3][2] = {{1, 64}, {1, 128}, {2, 128}};
     float best_ms = 1e30f;
     int rc = UG_OK;
-    for (int c = 0; c < 2 && rc == UG_OK; ++c) {
+    for (int c = 0; c < 3 && rc == UG_OK; ++c) {
         SweepOut o{};
         o.force = force;
-        launch_sweep(kSweepForce, w.sorted, w.start, w.geo, sa, o, cands[c], status, s);   // warm
+        auto sweep = [&]() {
+            if (cands[c][0] == 2)
+                launch_sweep2(kSweepForce, w.sorted, w.start, w.geo, sa, o, status, s, nullptr);
+            else
+                launch_sweep(kSweepForce, w.sorted, w.start, w.geo, sa, o, cands[c][1], status, s);
+        };
+        sweep();   // warm
         cudaEventRecord(e0, s);
-        for (int rep = 0; rep < 3; ++rep)
-            launch_sweep(kSweepForce, w.sorted, w.start, w.geo, sa, o, cands[c], status, s);
+        for (int rep = 0; rep < 3; ++rep) sweep();
         cudaEventRecord(e1, s);
         if (cudaEventSynchronize(e1) != cudaSuccess) { rc = UG_ECUDA; break; }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best_ms) { best_ms = ms; best->sweep_block = cands[c]; }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best->agents_per_lane = cands[c][0];
+            best->sweep_block = cands[c][1];
+        }
     }
     int32_t hst = 0;
     if (rc == UG_OK && cudaMemcpy(&hst, status, sizeof(hst), cudaMemcpyDeviceToHost) != cudaSuccess)

@@ -618,7 +618,7 @@ struct StepSaves {          // per-step records for the adjoint (nullable)
     ug_grid_info *geo;      // [nsteps][nsims]
 };
 int run_steps(float4 *state, uint32_t *perm, const SimArgs &sa, int nsteps, uint32_t max_boxes,
-              const Workspace &w, int sweep_block, const StepSaves *saves, int32_t *status,
-              cudaStream_t s, cudaEvent_t const *events = nullptr);
+              const Workspace &w, int sweep_block, int agents_per_lane, const StepSaves *saves,
+              int32_t *status, cudaStream_t s, cudaEvent_t const *events = nullptr);
 
 }  // namespace ug

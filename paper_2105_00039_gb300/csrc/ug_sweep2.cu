@@ -10,7 +10,8 @@
 // walked in warp lockstep (trip count = the warp's longest run) with clamped
 // indices and masks, candidates that pass the packed float32 pre-filter go to
 // per-agent lists, and the exact float-float contact test and Eq. 1 run in
-// warp-converged batches.  Single simulation only.
+// warp-converged batches.  A lane whose agents belong to different simulations
+// walks them separately, each with its own simulation's grid and constants.
 #include <cuda_runtime.h>
 
 #include "ug_internal.cuh"
@@ -40,47 +41,61 @@ __device__ __forceinline__ void add_contact(const float4 &me, const float4 &q, f
     ++a.np;
 }
 
-template <int MODE, int T>
-__global__ void __launch_bounds__(T, 8)
+template <int MODE, int T, bool MULTI>
+__global__ void __launch_bounds__(T, (MODE == kSweepStep && MULTI) ? 7 : 8)
 k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
          const ug_grid_info *__restrict__ geo, const uint32_t *__restrict__ skey, SimArgs sa,
          SweepOut out, int32_t *status) {
     __shared__ WarpLists2 wl[T / 32];
+    __shared__ uint32_t s_sims[2];
     chain_begin();
     if (cta_failed(status)) return;
     const int lane = threadIdx.x & 31;
     WarpLists2 &w = wl[threadIdx.x >> 5];
     const uint32_t n = sa.n;
-    const uint32_t i0 = (blockIdx.x * T + threadIdx.x) * 2u, i1 = i0 + 1u;
+    const uint32_t first = blockIdx.x * T * 2u;
+    const uint32_t i0 = first + threadIdx.x * 2u, i1 = i0 + 1u;
     const bool v0 = i0 < n, v1 = i1 < n;
-    const ug_params P = sa.pval;
-    const ug_grid_info g = geo[0];
-    const float m2 = 2.0f * P.contact_margin;
+    // simulations of the two agents (one lookup per CTA when the CTA's agents share one)
+    if (MULTI) {
+        if (threadIdx.x == 0) {
+            s_sims[0] = find_sim(sa, first);
+            s_sims[1] = find_sim(sa, min(first + 2u * T, n) - 1u);
+        }
+        __syncthreads();
+    }
+    const bool uniform = !MULTI || s_sims[0] == s_sims[1];
+    const uint32_t s0 = !MULTI ? 0u : uniform ? s_sims[0] : find_sim(sa, min(i0, n - 1u));
+    const uint32_t s1 = !MULTI ? 0u : uniform ? s_sims[0] : find_sim(sa, min(i1, n - 1u));
+    const ug_params P0 = sim_params(sa, s0);
+    const ug_params P1 = s1 == s0 ? P0 : sim_params(sa, s1);
+    const ug_grid_info g0 = geo[s0];
+    const ug_grid_info g1 = s1 == s0 ? g0 : geo[s1];
+    const float m20 = 2.0f * P0.contact_margin, m21 = 2.0f * P1.contact_margin;
     const float4 far = make_float4(1e30f, 1e30f, 1e30f, 1.0f);
     const float4 me0 = v0 ? __ldg(st + i0) : far;
     const float4 me1 = v1 ? __ldg(st + i1) : far;
     uint32_t k0 = 0, k1 = 0;
     if (v0) {
         int bx, by, bz;
-        k0 = skey ? __ldg(skey + i0) : box_key(me0, g, bx, by, bz);
+        k0 = skey ? __ldg(skey + i0) : box_key(me0, g0, bx, by, bz);
         k1 = k0;
-        if (v1) k1 = skey ? __ldg(skey + i1) : box_key(me1, g, bx, by, bz);
+        if (v1) k1 = skey ? __ldg(skey + i1) : box_key(me1, g1, bx, by, bz);
     }
-    const uint32_t dx = (uint32_t)g.dims[0];
-    const int plane = g.dims[0] * g.dims[1];
-    const bool split = v1 && ((k0 - g.box_base) / dx != (k1 - g.box_base) / dx);
-    const bool exact_diffs =
-        __all_sync(kFull, (!v0 || far_from_origin(me0, g.edge)) && (!v1 || far_from_origin(me1, g.edge)));
-    const FilterRow f0 = make_filter_row(me0, m2), f1 = make_filter_row(me1, m2);
+    const bool split = v1 && (s1 != s0 || (k0 - g0.box_base) / (uint32_t)g0.dims[0] !=
+                                             (k1 - g0.box_base) / (uint32_t)g0.dims[0]);
+    const bool exact_diffs = __all_sync(kFull, (!v0 || far_from_origin(me0, g0.edge)) &&
+                                                   (!v1 || far_from_origin(me1, g1.edge)));
+    const FilterRow f0 = make_filter_row(me0, m20), f1 = make_filter_row(me1, m21);
     Accum a0{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u}, a1{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u};
     int c0 = 0, c1 = 0;
     auto flush = [&]() {
         const int m0 = (int)__reduce_max_sync(kFull, (unsigned)c0);
         for (int k = 0; k < m0; ++k)
-            if (k < c0) add_contact(me0, __ldg(st + w.lst[0][k][lane]), m2, exact_diffs, P, a0);
+            if (k < c0) add_contact(me0, __ldg(st + w.lst[0][k][lane]), m20, exact_diffs, P0, a0);
         const int mm1 = (int)__reduce_max_sync(kFull, (unsigned)c1);
         for (int k = 0; k < mm1; ++k)
-            if (k < c1) add_contact(me1, __ldg(st + w.lst[1][k][lane]), m2, exact_diffs, P, a1);
+            if (k < c1) add_contact(me1, __ldg(st + w.lst[1][k][lane]), m21, exact_diffs, P1, a1);
         c0 = 0;
         c1 = 0;
     };
@@ -89,15 +104,16 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     for (int r = 0; r < nruns; ++r) {
         // runs 0..8 serve both agents (or agent 0 alone when split), 9..17 agent 1 when split
         const int rr = r < 9 ? r : r - 9;
-        const int off = (rr / 3 - 1) * plane + (rr % 3 - 1) * (int)dx;
-        bool s0 = false, s1 = false;
+        bool s0on = false, s1on = false;
         uint32_t b = v0 ? i0 : 0u;     // a row that exists; masked off when len == 0
         int len = 0;
         if (v0 && (r < 9 || split)) {
             uint32_t lo, hi;
-            if (!split) { lo = k0; hi = k1; s0 = true; s1 = v1; }
-            else if (r < 9) { lo = k0; hi = k0; s0 = true; }
-            else { lo = k1; hi = k1; s1 = true; }
+            const ug_grid_info &g = r < 9 ? g0 : g1;
+            if (!split) { lo = k0; hi = k1; s0on = true; s1on = v1; }
+            else if (r < 9) { lo = k0; hi = k0; s0on = true; }
+            else { lo = k1; hi = k1; s1on = true; }
+            const int off = (rr / 3 - 1) * g.dims[0] * g.dims[1] + (rr % 3 - 1) * g.dims[0];
             b = __ldg(start + (uint32_t)((int)lo + off) - 1u);
             len = (int)(__ldg(start + (uint32_t)((int)hi + off) + 2u) - b);
             if (len == 0) b = i0;
@@ -110,11 +126,11 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
                 const uint32_t jc = b + (uint32_t)min(t + u, last);
                 const float4 q = __ldg(st + jc);
                 const bool in = t + u < len;
-                if (in & s0 & (jc != i0) & prefilter(q, f0)) {
+                if (in & s0on & (jc != i0) & prefilter(q, f0)) {
                     w.lst[0][c0][lane] = jc;
                     ++c0;
                 }
-                if (in & s1 & (jc != i1) & prefilter(q, f1)) {
+                if (in & s1on & (jc != i1) & prefilter(q, f1)) {
                     w.lst[1][c1][lane] = jc;
                     ++c1;
                 }
@@ -136,7 +152,7 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     float4 n0 = me0, n1 = me1;
     if (v0) {
         bool mv, cp;
-        const float3 u = displacement(F0.x, F0.y, F0.z, me0.w, P, &mv, &cp);
+        const float3 u = displacement(F0.x, F0.y, F0.z, me0.w, P0, &mv, &cp);
         n0 = make_float4(me0.x + u.x, me0.y + u.y, me0.z + u.z, me0.w);
         out.state_out[i0] = n0;
         if (out.force) out.force[i0] = make_float4(F0.x, F0.y, F0.z, (mv ? 1.f : 0.f) + (cp ? 2.f : 0.f));
@@ -144,7 +160,7 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     }
     if (v1) {
         bool mv, cp;
-        const float3 u = displacement(F1.x, F1.y, F1.z, me1.w, P, &mv, &cp);
+        const float3 u = displacement(F1.x, F1.y, F1.z, me1.w, P1, &mv, &cp);
         n1 = make_float4(me1.x + u.x, me1.y + u.y, me1.z + u.z, me1.w);
         out.state_out[i1] = n1;
         if (out.force) out.force[i1] = make_float4(F1.x, F1.y, F1.z, (mv ? 1.f : 0.f) + (cp ? 2.f : 0.f));
@@ -152,9 +168,14 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     }
     bounds_codes(n0, v0, codes);
     bounds_codes(n1, v1, c2);
+    if (uniform) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) codes[k] = max(codes[k], c2[k]);
-    accumulate_bounds_codes(sa, codes, v0, 0u, true, out.bounds);
+        for (int k = 0; k < 8; ++k) codes[k] = max(codes[k], c2[k]);
+        accumulate_bounds_codes(sa, codes, v0, s0, true, out.bounds);
+    } else {
+        accumulate_bounds_codes(sa, codes, v0, s0, false, out.bounds);
+        accumulate_bounds_codes(sa, c2, v1, s1, false, out.bounds);
+    }
     if (elect_last_cta(&out.ctrl->done))
         finalize_grid(sa, out.bounds, out.geo_next, out.ctrl, out.max_boxes, status);
 }
@@ -164,10 +185,22 @@ void launch_sweep2(int mode, const float4 *sorted, const uint32_t *start, const 
                    const uint32_t *skey) {
     constexpr int T = 128;
     const unsigned grid = (unsigned)((sa.n + 2 * T - 1) / (2 * T));
-    if (mode == kSweepForce)
-        launch_chained(k_sweep2<kSweepForce, T>, grid, T, s, sorted, start, geo, skey, sa, out, status);
-    else
-        launch_chained(k_sweep2<kSweepStep, T>, grid, T, s, sorted, start, geo, skey, sa, out, status);
+    const bool multi = sa.nsims > 1;
+    if (mode == kSweepForce) {
+        if (multi)
+            launch_chained(k_sweep2<kSweepForce, T, true>, grid, T, s, sorted, start, geo, skey, sa,
+                           out, status);
+        else
+            launch_chained(k_sweep2<kSweepForce, T, false>, grid, T, s, sorted, start, geo, skey, sa,
+                           out, status);
+    } else {
+        if (multi)
+            launch_chained(k_sweep2<kSweepStep, T, true>, grid, T, s, sorted, start, geo, skey, sa,
+                           out, status);
+        else
+            launch_chained(k_sweep2<kSweepStep, T, false>, grid, T, s, sorted, start, geo, skey, sa,
+                           out, status);
+    }
 }
 
 }  // namespace ug

@@ -289,7 +289,19 @@ def test_autotuner_picks_a_valid_block(U):
     x = _gpu(st)
     pdev = torch.stack([U.Params().as_tensor(DEV) for _ in range(6)])
     best = U.tune_batched(x, torch.from_numpy(offs.astype(np.int32)).to(DEV), pdev, 6, 2_000_000)
-    assert best.sweep_block in (64, 128)
+    assert (best.agents_per_lane, best.sweep_block) in ((1, 64), (1, 128), (2, 128))
+    # every configuration gives the same bits
+    outs = []
+    for apl, blk in ((1, 64), (1, 128), (2, 128)):
+        t = U.ug_tuning()
+        t.agents_per_lane, t.sweep_block = apl, blk
+        y = x.clone()
+        perm = U.iota(len(st), x.device)
+        sp = U.Stepper(len(st), 2_000_000, x.device, nsims=6)
+        sp.step_batched(y, perm, torch.from_numpy(offs.astype(np.int32)).to(DEV), pdev, 3, t)
+        sp.check("tuned")
+        outs.append(y.cpu().numpy())
+    assert all(np.array_equal(outs[0], o) for o in outs[1:])
 
 
 # ------------------------------------------------------------------ edge cases
