@@ -10,8 +10,9 @@
 // walked in warp lockstep (trip count = the warp's longest run) with clamped
 // indices and masks, candidates that pass the packed float32 pre-filter go to
 // per-agent lists, and the exact float-float contact test and Eq. 1 run in
-// warp-converged batches.  A lane whose agents belong to different simulations
-// walks them separately, each with its own simulation's grid and constants.
+// warp-converged batches.  k_sweep2 serves one simulation; k_sweep2m serves
+// many (a lane whose agents belong to different simulations walks them
+// separately, each with its own simulation's grid and constants).
 #include <cuda_runtime.h>
 
 #include "ug_internal.cuh"
@@ -41,9 +42,128 @@ __device__ __forceinline__ void add_contact(const float4 &me, const float4 &q, f
     ++a.np;
 }
 
+template <int MODE, int T>
+__global__ void __launch_bounds__(T, 8)
+k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
+         const ug_grid_info *__restrict__ geo, const uint32_t *__restrict__ skey, SimArgs sa,
+         SweepOut out, int32_t *status) {
+    __shared__ WarpLists2 wl[T / 32];
+    chain_begin();
+    if (cta_failed(status)) return;
+    const int lane = threadIdx.x & 31;
+    WarpLists2 &w = wl[threadIdx.x >> 5];
+    const uint32_t n = sa.n;
+    const uint32_t i0 = (blockIdx.x * T + threadIdx.x) * 2u, i1 = i0 + 1u;
+    const bool v0 = i0 < n, v1 = i1 < n;
+    const ug_params P = sa.pval;
+    const ug_grid_info g = geo[0];
+    const float m2 = 2.0f * P.contact_margin;
+    const float4 far = make_float4(1e30f, 1e30f, 1e30f, 1.0f);
+    const float4 me0 = v0 ? __ldg(st + i0) : far;
+    const float4 me1 = v1 ? __ldg(st + i1) : far;
+    uint32_t k0 = 0, k1 = 0;
+    if (v0) {
+        int bx, by, bz;
+        k0 = skey ? __ldg(skey + i0) : box_key(me0, g, bx, by, bz);
+        k1 = k0;
+        if (v1) k1 = skey ? __ldg(skey + i1) : box_key(me1, g, bx, by, bz);
+    }
+    const uint32_t dx = (uint32_t)g.dims[0];
+    const int plane = g.dims[0] * g.dims[1];
+    const bool split = v1 && ((k0 - g.box_base) / dx != (k1 - g.box_base) / dx);
+    const bool exact_diffs =
+        __all_sync(kFull, (!v0 || far_from_origin(me0, g.edge)) && (!v1 || far_from_origin(me1, g.edge)));
+    const FilterRow f0 = make_filter_row(me0, m2), f1 = make_filter_row(me1, m2);
+    Accum a0{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u}, a1{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u};
+    int c0 = 0, c1 = 0;
+    auto flush = [&]() {
+        const int m0 = (int)__reduce_max_sync(kFull, (unsigned)c0);
+        for (int k = 0; k < m0; ++k)
+            if (k < c0) add_contact(me0, __ldg(st + w.lst[0][k][lane]), m2, exact_diffs, P, a0);
+        const int mm1 = (int)__reduce_max_sync(kFull, (unsigned)c1);
+        for (int k = 0; k < mm1; ++k)
+            if (k < c1) add_contact(me1, __ldg(st + w.lst[1][k][lane]), m2, exact_diffs, P, a1);
+        c0 = 0;
+        c1 = 0;
+    };
+    const int nruns = __any_sync(kFull, split) ? 18 : 9;
+#pragma unroll 1
+    for (int r = 0; r < nruns; ++r) {
+        // runs 0..8 serve both agents (or agent 0 alone when split), 9..17 agent 1 when split
+        const int rr = r < 9 ? r : r - 9;
+        const int off = (rr / 3 - 1) * plane + (rr % 3 - 1) * (int)dx;
+        bool s0 = false, s1 = false;
+        uint32_t b = v0 ? i0 : 0u;     // a row that exists; masked off when len == 0
+        int len = 0;
+        if (v0 && (r < 9 || split)) {
+            uint32_t lo, hi;
+            if (!split) { lo = k0; hi = k1; s0 = true; s1 = v1; }
+            else if (r < 9) { lo = k0; hi = k0; s0 = true; }
+            else { lo = k1; hi = k1; s1 = true; }
+            b = __ldg(start + (uint32_t)((int)lo + off) - 1u);
+            len = (int)(__ldg(start + (uint32_t)((int)hi + off) + 2u) - b);
+            if (len == 0) b = i0;
+        }
+        const int last = max(len - 1, 0);
+        const int lmax = (int)__reduce_max_sync(kFull, (unsigned)len);
+        for (int t = 0; t < lmax; t += kSweepUnroll) {
+#pragma unroll
+            for (int u = 0; u < kSweepUnroll; ++u) {
+                const uint32_t jc = b + (uint32_t)min(t + u, last);
+                const float4 q = __ldg(st + jc);
+                const bool in = t + u < len;
+                if (in & s0 & (jc != i0) & prefilter(q, f0)) {
+                    w.lst[0][c0][lane] = jc;
+                    ++c0;
+                }
+                if (in & s1 & (jc != i1) & prefilter(q, f1)) {
+                    w.lst[1][c1][lane] = jc;
+                    ++c1;
+                }
+            }
+            if (__any_sync(kFull, max(c0, c1) > kListCap - kSweepUnroll)) flush();
+        }
+    }
+    flush();
+
+    const float3 F0 = make_float3(a0.sx + a0.cx, a0.sy + a0.cy, a0.sz + a0.cz);
+    const float3 F1 = make_float3(a1.sx + a1.cx, a1.sy + a1.cy, a1.sz + a1.cz);
+    if (MODE == kSweepForce) {
+        if (v0) out.force[i0] = make_float4(F0.x, F0.y, F0.z, (float)a0.np);
+        if (v1) out.force[i1] = make_float4(F1.x, F1.y, F1.z, (float)a1.np);
+        return;
+    }
+    // fused step: Sec. III adherence / integration / cap, then move
+    uint32_t codes[8], c2[8];
+    float4 n0 = me0, n1 = me1;
+    if (v0) {
+        bool mv, cp;
+        const float3 u = displacement(F0.x, F0.y, F0.z, me0.w, P, &mv, &cp);
+        n0 = make_float4(me0.x + u.x, me0.y + u.y, me0.z + u.z, me0.w);
+        out.state_out[i0] = n0;
+        if (out.force) out.force[i0] = make_float4(F0.x, F0.y, F0.z, (mv ? 1.f : 0.f) + (cp ? 2.f : 0.f));
+        if (!row_ok(n0)) set_status(status, UG_EBADSTATE);
+    }
+    if (v1) {
+        bool mv, cp;
+        const float3 u = displacement(F1.x, F1.y, F1.z, me1.w, P, &mv, &cp);
+        n1 = make_float4(me1.x + u.x, me1.y + u.y, me1.z + u.z, me1.w);
+        out.state_out[i1] = n1;
+        if (out.force) out.force[i1] = make_float4(F1.x, F1.y, F1.z, (mv ? 1.f : 0.f) + (cp ? 2.f : 0.f));
+        if (!row_ok(n1)) set_status(status, UG_EBADSTATE);
+    }
+    bounds_codes(n0, v0, codes);
+    bounds_codes(n1, v1, c2);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) codes[k] = max(codes[k], c2[k]);
+    accumulate_bounds_codes(sa, codes, v0, 0u, true, out.bounds);
+    if (elect_last_cta(&out.ctrl->done))
+        finalize_grid(sa, out.bounds, out.geo_next, out.ctrl, out.max_boxes, status);
+}
+
 template <int MODE, int T, bool MULTI>
 __global__ void __launch_bounds__(T, (MODE == kSweepStep && MULTI) ? 7 : 8)
-k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
+k_sweep2m(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
          const ug_grid_info *__restrict__ geo, const uint32_t *__restrict__ skey, SimArgs sa,
          SweepOut out, int32_t *status) {
     __shared__ WarpLists2 wl[T / 32];
@@ -185,21 +305,20 @@ void launch_sweep2(int mode, const float4 *sorted, const uint32_t *start, const 
                    const uint32_t *skey) {
     constexpr int T = 128;
     const unsigned grid = (unsigned)((sa.n + 2 * T - 1) / (2 * T));
-    const bool multi = sa.nsims > 1;
-    if (mode == kSweepForce) {
-        if (multi)
-            launch_chained(k_sweep2<kSweepForce, T, true>, grid, T, s, sorted, start, geo, skey, sa,
+    if (sa.nsims > 1) {
+        if (mode == kSweepForce)
+            launch_chained(k_sweep2m<kSweepForce, T, true>, grid, T, s, sorted, start, geo, skey, sa,
                            out, status);
         else
-            launch_chained(k_sweep2<kSweepForce, T, false>, grid, T, s, sorted, start, geo, skey, sa,
+            launch_chained(k_sweep2m<kSweepStep, T, true>, grid, T, s, sorted, start, geo, skey, sa,
                            out, status);
     } else {
-        if (multi)
-            launch_chained(k_sweep2<kSweepStep, T, true>, grid, T, s, sorted, start, geo, skey, sa,
-                           out, status);
+        if (mode == kSweepForce)
+            launch_chained(k_sweep2<kSweepForce, T>, grid, T, s, sorted, start, geo, skey, sa, out,
+                           status);
         else
-            launch_chained(k_sweep2<kSweepStep, T, false>, grid, T, s, sorted, start, geo, skey, sa,
-                           out, status);
+            launch_chained(k_sweep2<kSweepStep, T>, grid, T, s, sorted, start, geo, skey, sa, out,
+                           status);
     }
 }
 
