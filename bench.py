@@ -461,7 +461,8 @@ def measure_batched(dev, flush, nsims=256, nsteps=50, reps=3):
             "batched_agent_steps_per_s": n * nsteps / (t_batched / 1e3),
             "sequential_agent_steps_per_s": n * nsteps / (t_seq / 1e3),
             "speedup": t_seq / t_batched, "bit_identical_to_plain": bool(same),
-            "tuned_sweep_block": int(tune.sweep_block)}
+            "tuned_sweep_block": int(tune.sweep_block),
+            "tuned_agents_per_lane": int(tune.agents_per_lane)}
 
 
 def measure_adjoint(dev, flush, side=64, nsteps=50, ckpt=10, reps=3):
@@ -545,9 +546,21 @@ def measure_density(dev, flush, reps=2, nsteps=20):
         sp.check("density")
         per_step_s = ms / 1e3 / nsteps
         alg = BYTES_PER_AGENT_STEP * n + BYTES_PER_BOX * mb / 1.05
+        # one traced pass for the per-kernel split (events un-chain the kernels)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 + 5 * nsteps)]
+        for e in ev:
+            e.record()
+        x.copy_(x0)
+        U._check(lib.ug_iota(U._ptr(perm), n, U._stream()), "ug_iota")
+        sp.step_traced(x, perm, prm, nsteps, ev)
+        ev[-1].synchronize()
+        names = ("key", "scan", "place", "canon", "sweep")
+        split = {nm: sum(ev[1 + 5 * t + j].elapsed_time(ev[2 + 5 * t + j]) for t in range(nsteps))
+                 * 1000.0 / nsteps for j, nm in enumerate(names)}
         rows.append({"n_agents": n, "mean_neighbours_target": nbar,
                      "agent_steps_per_s": n * nsteps / (ms / 1e3), "ms_per_step": per_step_s * 1e3,
-                     "step_alg_gbs": alg / per_step_s / 1e9, "step_hbm_frac": alg / per_step_s / 1e9 / hbm})
+                     "step_alg_gbs": alg / per_step_s / 1e9, "step_hbm_frac": alg / per_step_s / 1e9 / hbm,
+                     "kernel_us_per_step_traced": split})
         del x0, x, perm, sp
         torch.cuda.empty_cache()
     return rows

@@ -58,6 +58,12 @@ const char *ug_strerror(int status);
 /* Library ABI version (major * 10000 + minor * 100 + patch). */
 int ug_version(void);
 
+/* Fault injection for tests: set the process-wide bound on the polls of the
+ * grid scan's bounded waits (default 4194304) and return the previous bound.
+ * With 0, a scan tile that finds a predecessor not yet published gives up at
+ * once and reports UG_ETIMEOUT instead of waiting; nothing ever hangs. */
+uint32_t ug_debug_spin_limit(uint32_t limit);
+
 /* ------------------------------------------------------------------ types */
 
 /* Mechanical constants.  k and gamma are Eq. 1's repulsion and attraction

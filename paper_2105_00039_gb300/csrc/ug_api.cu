@@ -154,6 +154,8 @@ const char *ug_strerror(int status) {
 
 int ug_version(void) { return 10000; }
 
+uint32_t ug_debug_spin_limit(uint32_t limit) { return set_spin_limit(limit); }
+
 size_t ug_workspace_bytes(uint32_t n, uint32_t nsims, uint32_t max_boxes) {
     Workspace w;
     return layout_workspace(nullptr, n, nsims == 0 ? 1 : nsims, max_boxes, &w);

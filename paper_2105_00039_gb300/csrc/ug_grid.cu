@@ -17,6 +17,8 @@
 //             smaller input index), gathering rows and ids into that slot
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "ug_internal.cuh"
 
 namespace ug {
@@ -95,7 +97,8 @@ __device__ __forceinline__ void publish(unsigned long long *st, uint32_t t, uint
 // back to the nearest tile that already knows its inclusive prefix.  Waits are
 // bounded; on timeout the error is recorded and the partial sum returned so
 // that successors finish too.
-__device__ uint32_t look_back_warp(unsigned long long *st, uint32_t t, int32_t *status) {
+__device__ uint32_t look_back_warp(unsigned long long *st, uint32_t t, uint32_t spin_limit,
+                                   int32_t *status) {
     const int lane = threadIdx.x & 31;
     uint32_t excl = 0;
     int j = (int)t - 1 - lane;
@@ -105,7 +108,7 @@ __device__ uint32_t look_back_warp(unsigned long long *st, uint32_t t, int32_t *
             j >= 0 ? *(volatile unsigned long long *)(st + j) : (2ull << 32);
         const uint32_t flag = (uint32_t)(w >> 32);
         if (__any_sync(kFull, flag == 0u)) {
-            if (++spins > kSpinLimit || peek_status(status) != 0) {
+            if (++spins > spin_limit || peek_status(status) != 0) {
                 set_status(status, UG_ETIMEOUT);
                 return excl;
             }
@@ -122,7 +125,7 @@ __device__ uint32_t look_back_warp(unsigned long long *st, uint32_t t, int32_t *
 
 __global__ void __launch_bounds__(kScanThreads)
 k_scan(uint32_t *__restrict__ counts, uint32_t *__restrict__ start, Ctrl *ctrl,
-       unsigned long long *tstat, int32_t *status) {
+       unsigned long long *tstat, uint32_t spin_limit, int32_t *status) {
     __shared__ uint32_t s_tile, s_prefix;
     __shared__ uint32_t s_warp[kScanThreads / 32];
     chain_begin();
@@ -172,7 +175,7 @@ k_scan(uint32_t *__restrict__ counts, uint32_t *__restrict__ start, Ctrl *ctrl,
                 if (lane == 0) publish(tstat, t, 2u, tile_total);
             } else {
                 if (lane == 0) publish(tstat, t, 1u, tile_total);
-                excl = look_back_warp(tstat, t, status);
+                excl = look_back_warp(tstat, t, spin_limit, status);
                 if (lane == 0) publish(tstat, t, 2u, excl + tile_total);
             }
             if (lane == 0) s_prefix = excl;
@@ -241,6 +244,11 @@ k_canon(const uint32_t *__restrict__ tmp, const uint32_t *__restrict__ key,
 // ------------------------------------------------------------------ launchers
 static inline unsigned blocks_for(uint32_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Bound on the look-back polls of the scan, process-wide (see ug_debug_spin_limit).
+static std::atomic<uint32_t> g_spin_limit{kSpinLimit};
+uint32_t spin_limit() { return g_spin_limit.load(std::memory_order_relaxed); }
+uint32_t set_spin_limit(uint32_t v) { return g_spin_limit.exchange(v); }
+
 void launch_bounds(const float4 *st, const SimArgs &sa, const Workspace &w, ug_grid_info *geo,
                    uint32_t max_boxes, int32_t *status, cudaStream_t s) {
     launch_chained(k_bounds, blocks_for(sa.n, 256), 256, s, st, sa, w.bounds, geo, w.ctrl,
@@ -258,7 +266,7 @@ void launch_scan(const Workspace &w, uint32_t *start, uint32_t max_boxes, int32_
     (void)max_boxes;
     const unsigned grid = (unsigned)min((int)w.ntiles, 2 * device_sm_count());
     launch_chained(k_scan, grid > 0 ? grid : 1u, (unsigned)kScanThreads, s, w.counts, start, w.ctrl,
-                   w.scan_status, status);
+                   w.scan_status, spin_limit(), status);
 }
 
 void launch_place(const Workspace &w, const uint32_t *start, uint32_t n, int32_t *status,

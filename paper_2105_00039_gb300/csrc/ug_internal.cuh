@@ -573,6 +573,8 @@ int device_sm_count();
 
 // ------------------------------------------------------------------ launchers
 // Grid build pieces (ug_grid.cu).  All asynchronous on `s`.
+uint32_t spin_limit();
+uint32_t set_spin_limit(uint32_t v);
 void launch_bounds(const float4 *st, const SimArgs &sa, const Workspace &w, ug_grid_info *geo,
                    uint32_t max_boxes, int32_t *status, cudaStream_t s);
 void launch_key(const float4 *st, const SimArgs &sa, const Workspace &w, const ug_grid_info *geo,

@@ -1,0 +1,81 @@
+"""Failure detection on the GPU, injected from the host: every error becomes a
+status code, later kernels of the call do nothing, and the context stays usable.
+No test faults, traps or hangs a GPU."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2105_00039_gb300 import populations as P
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module")
+def U():
+    from paper_2105_00039_gb300 import ugmech
+    ugmech.load()
+    return ugmech
+
+
+def _healthy(U):
+    st = P.small_uniform(1)
+    x = torch.from_numpy(st).to(DEV)
+    srt, perm, start, info, status = U.grid_build(x)
+    F = U.compute_forces(srt, start, info)
+    assert int(status.item()) == 0 and torch.isfinite(F).all()
+
+
+def test_scan_wait_timeout_is_reported_not_hung(U):
+    lib = U.load()
+    st = P.density_cube(1 << 21, 2.0, seed=21)          # ~2.6M boxes: hundreds of scan tiles
+    x = torch.from_numpy(st).to(DEV)
+    prev = lib.ug_debug_spin_limit(0)
+    try:
+        codes = set()
+        for _ in range(3):
+            _, _, _, _, status = U.grid_build(x, check=False)
+            codes.add(int(status.item()))
+    finally:
+        lib.ug_debug_spin_limit(prev)
+    assert codes <= {U.UG_OK, U.UG_ETIMEOUT}
+    _healthy(U)
+
+
+def test_error_stops_the_rest_of_the_call(U):
+    st = P.small_uniform(2)
+    st[5, 0] = np.nan
+    x = torch.from_numpy(st).to(DEV)
+    n = len(st)
+    sp = U.Stepper(n, 100000, x.device)
+    perm = U.iota(n, x.device)
+    before = x.clone()
+    sp.step(x, perm, U.Params(), 5)
+    with pytest.raises(U.UgError) as e:
+        sp.check()
+    assert e.value.code == U.UG_EBADSTATE
+    assert torch.equal(x[~torch.isnan(x)], before[~torch.isnan(before)])   # rows untouched
+    _healthy(U)
+
+
+def test_preset_status_makes_calls_no_ops(U):
+    st = P.small_uniform(3)
+    x = torch.from_numpy(st).to(DEV)
+    status = U.new_status(DEV)
+    status.fill_(U.UG_ECAPACITY)                          # an earlier error in the same call chain
+    srt, perm, start, info, status = U.grid_build(x, status=status, check=False)
+    assert int(status.item()) == U.UG_ECAPACITY
+    assert int(start.abs().sum().item()) == 0             # nothing was written
+    _healthy(U)
+
+
+def test_workspace_too_small_is_rejected_on_the_host(U):
+    lib = U.load()
+    st = P.small_uniform(4)
+    x = torch.from_numpy(st).to(DEV)
+    ws = torch.empty(1024, dtype=torch.uint8, device=DEV)
+    perm = U.iota(len(st), x.device)
+    status = U.new_status(DEV)
+    rc = lib.ug_step(U._ptr(x), U._ptr(perm), len(st), U.Params().c(), 1, 10000, U._ptr(ws),
+                     ws.numel(), U._ptr(status), U._stream())
+    assert rc == U.UG_EWORKSPACE and int(status.item()) == 0
