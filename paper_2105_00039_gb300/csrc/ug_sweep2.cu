@@ -87,36 +87,21 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
         c1 = 0;
     };
     const int nruns = __any_sync(kFull, split) ? 18 : 9;
-    // the box-table bounds of run r (two start[] reads), fetched one run ahead
-    // so that their latency hides behind the previous run's candidates
-    auto fetch = [&](int r, uint32_t &blo, uint32_t &bhi) {
-        blo = 0u;
-        bhi = 0u;
-        if (v0 && (r < 9 || split)) {
-            const int rr = r < 9 ? r : r - 9;
-            const int off = (rr / 3 - 1) * plane + (rr % 3 - 1) * (int)dx;
-            const uint32_t lo = (split && r >= 9) ? k1 : k0;
-            const uint32_t hi = split ? lo : k1;
-            blo = __ldg(start + (uint32_t)((int)lo + off) - 1u);
-            bhi = __ldg(start + (uint32_t)((int)hi + off) + 2u);
-        }
-    };
-    uint32_t nlo, nhi;
-    fetch(0, nlo, nhi);
 #pragma unroll 1
     for (int r = 0; r < nruns; ++r) {
         // runs 0..8 serve both agents (or agent 0 alone when split), 9..17 agent 1 when split
-        const uint32_t clo = nlo, chi = nhi;
-        if (r + 1 < nruns) fetch(r + 1, nlo, nhi);
+        const int rr = r < 9 ? r : r - 9;
+        const int off = (rr / 3 - 1) * plane + (rr % 3 - 1) * (int)dx;
         bool s0 = false, s1 = false;
         uint32_t b = v0 ? i0 : 0u;     // a row that exists; masked off when len == 0
         int len = 0;
         if (v0 && (r < 9 || split)) {
-            if (!split) { s0 = true; s1 = v1; }
-            else if (r < 9) s0 = true;
-            else s1 = true;
-            b = clo;
-            len = (int)(chi - clo);
+            uint32_t lo, hi;
+            if (!split) { lo = k0; hi = k1; s0 = true; s1 = v1; }
+            else if (r < 9) { lo = k0; hi = k0; s0 = true; }
+            else { lo = k1; hi = k1; s1 = true; }
+            b = __ldg(start + (uint32_t)((int)lo + off) - 1u);
+            len = (int)(__ldg(start + (uint32_t)((int)hi + off) + 2u) - b);
             if (len == 0) b = i0;
         }
         const int last = max(len - 1, 0);
@@ -235,36 +220,22 @@ k_sweep2m(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
         c1 = 0;
     };
     const int nruns = __any_sync(kFull, split) ? 18 : 9;
-    // the box-table bounds of run r, fetched one run ahead (see k_sweep2)
-    auto fetch = [&](int r, uint32_t &blo, uint32_t &bhi) {
-        blo = 0u;
-        bhi = 0u;
-        if (v0 && (r < 9 || split)) {
-            const int rr = r < 9 ? r : r - 9;
-            const ug_grid_info &g = r < 9 ? g0 : g1;
-            const int off = (rr / 3 - 1) * g.dims[0] * g.dims[1] + (rr % 3 - 1) * g.dims[0];
-            const uint32_t lo = (split && r >= 9) ? k1 : k0;
-            const uint32_t hi = split ? lo : k1;
-            blo = __ldg(start + (uint32_t)((int)lo + off) - 1u);
-            bhi = __ldg(start + (uint32_t)((int)hi + off) + 2u);
-        }
-    };
-    uint32_t nlo, nhi;
-    fetch(0, nlo, nhi);
 #pragma unroll 1
     for (int r = 0; r < nruns; ++r) {
         // runs 0..8 serve both agents (or agent 0 alone when split), 9..17 agent 1 when split
-        const uint32_t clo = nlo, chi = nhi;
-        if (r + 1 < nruns) fetch(r + 1, nlo, nhi);
+        const int rr = r < 9 ? r : r - 9;
         bool s0on = false, s1on = false;
         uint32_t b = v0 ? i0 : 0u;     // a row that exists; masked off when len == 0
         int len = 0;
         if (v0 && (r < 9 || split)) {
-            if (!split) { s0on = true; s1on = v1; }
-            else if (r < 9) s0on = true;
-            else s1on = true;
-            b = clo;
-            len = (int)(chi - clo);
+            uint32_t lo, hi;
+            const ug_grid_info &g = r < 9 ? g0 : g1;
+            if (!split) { lo = k0; hi = k1; s0on = true; s1on = v1; }
+            else if (r < 9) { lo = k0; hi = k0; s0on = true; }
+            else { lo = k1; hi = k1; s1on = true; }
+            const int off = (rr / 3 - 1) * g.dims[0] * g.dims[1] + (rr % 3 - 1) * g.dims[0];
+            b = __ldg(start + (uint32_t)((int)lo + off) - 1u);
+            len = (int)(__ldg(start + (uint32_t)((int)hi + off) + 2u) - b);
             if (len == 0) b = i0;
         }
         const int last = max(len - 1, 0);
