@@ -19,15 +19,8 @@
 
 namespace ug {
 
-constexpr int kListCap2 = 12;
-
 struct WarpLists2 {
     uint32_t lst[2][kListCap][32];
-};
-
-struct WarpRuns2 {                 // per-warp scratch of the flattened single-simulation sweep
-    uint32_t lst[2][kListCap2][32];
-    uint2 runs[18][32];            // this lane's non-empty runs: first slot, end slot
 };
 
 struct Accum {
@@ -54,11 +47,11 @@ __global__ void __launch_bounds__(T, 8)
 k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
          const ug_grid_info *__restrict__ geo, const uint32_t *__restrict__ skey, SimArgs sa,
          SweepOut out, int32_t *status) {
-    __shared__ WarpRuns2 wl[T / 32];
+    __shared__ WarpLists2 wl[T / 32];
     chain_begin();
     if (cta_failed(status)) return;
     const int lane = threadIdx.x & 31;
-    WarpRuns2 &w = wl[threadIdx.x >> 5];
+    WarpLists2 &w = wl[threadIdx.x >> 5];
     const uint32_t n = sa.n;
     const uint32_t i0 = (blockIdx.x * T + threadIdx.x) * 2u, i1 = i0 + 1u;
     const bool v0 = i0 < n, v1 = i1 < n;
@@ -93,71 +86,43 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
         c0 = 0;
         c1 = 0;
     };
-    // this lane's non-empty runs: 0..8 serve both agents (agent 0 alone when
-    // split), then, when split, agent 1's own 9 runs; nr0 of them are agent 0's
-    int nr = 0, nr0 = 0, total = 0;
-    if (v0) {
+    const int nruns = __any_sync(kFull, split) ? 18 : 9;
+#pragma unroll 1
+    for (int r = 0; r < nruns; ++r) {
+        // runs 0..8 serve both agents (or agent 0 alone when split), 9..17 agent 1 when split
+        const int rr = r < 9 ? r : r - 9;
+        const int off = (rr / 3 - 1) * plane + (rr % 3 - 1) * (int)dx;
+        bool s0 = false, s1 = false;
+        uint32_t b = v0 ? i0 : 0u;     // a row that exists; masked off when len == 0
+        int len = 0;
+        if (v0 && (r < 9 || split)) {
+            uint32_t lo, hi;
+            if (!split) { lo = k0; hi = k1; s0 = true; s1 = v1; }
+            else if (r < 9) { lo = k0; hi = k0; s0 = true; }
+            else { lo = k1; hi = k1; s1 = true; }
+            b = __ldg(start + (uint32_t)((int)lo + off) - 1u);
+            len = (int)(__ldg(start + (uint32_t)((int)hi + off) + 2u) - b);
+            if (len == 0) b = i0;
+        }
+        const int last = max(len - 1, 0);
+        const int lmax = (int)__reduce_max_sync(kFull, (unsigned)len);
+        for (int t = 0; t < lmax; t += kSweepUnroll) {
 #pragma unroll
-        for (int r = 0; r < 18; ++r) {
-            if (r < 9 || split) {
-                const int rr = r < 9 ? r : r - 9;
-                const int off = (rr / 3 - 1) * plane + (rr % 3 - 1) * (int)dx;
-                const uint32_t lo = (split && r >= 9) ? k1 : k0;
-                const uint32_t hi = split ? lo : k1;
-                const uint32_t rb = __ldg(start + (uint32_t)((int)lo + off) - 1u);
-                const uint32_t re = __ldg(start + (uint32_t)((int)hi + off) + 2u);
-                if (re > rb) {
-                    w.runs[nr][lane] = make_uint2(rb, re);
-                    ++nr;
-                    total += (int)(re - rb);
+            for (int u = 0; u < kSweepUnroll; ++u) {
+                const uint32_t jc = b + (uint32_t)min(t + u, last);
+                const float4 q = __ldg(st + jc);
+                const bool in = t + u < len;
+                if (in & s0 & (jc != i0) & prefilter(q, f0)) {
+                    w.lst[0][c0][lane] = jc;
+                    ++c0;
+                }
+                if (in & s1 & (jc != i1) & prefilter(q, f1)) {
+                    w.lst[1][c1][lane] = jc;
+                    ++c1;
                 }
             }
-            if (r == 8) nr0 = nr;
+            if (__any_sync(kFull, max(c0, c1) > kListCap - kSweepUnroll)) flush();
         }
-    }
-    // walk the runs back to back: a warp's trip count is its largest total; a
-    // lane that has finished keeps reading its own row with both agents off
-    const uint32_t self = v0 ? i0 : 0u;
-    int r = 0;
-    uint32_t j = self, jend = self + 1u;
-    bool on0 = false, on1 = false;
-    if (nr > 0) {
-        const uint2 c = w.runs[0][lane];
-        j = c.x;
-        jend = c.y;
-        on0 = !split || nr0 > 0;
-        on1 = v1 && (!split || nr0 == 0);
-    }
-    const int tmax = (int)__reduce_max_sync(kFull, (unsigned)total);
-    for (int t = 0; t < tmax; t += kSweepUnroll) {
-#pragma unroll
-        for (int u = 0; u < kSweepUnroll; ++u) {
-            const uint32_t jc = j;
-            const float4 q = __ldg(st + jc);
-            if (on0 & (jc != i0) & prefilter(q, f0)) {
-                w.lst[0][c0][lane] = jc;
-                ++c0;
-            }
-            if (on1 & (jc != i1) & prefilter(q, f1)) {
-                w.lst[1][c1][lane] = jc;
-                ++c1;
-            }
-            if (++j == jend) {
-                if (++r < nr) {
-                    const uint2 c = w.runs[r][lane];
-                    j = c.x;
-                    jend = c.y;
-                    on0 = !split || r < nr0;
-                    on1 = v1 && (!split || r >= nr0);
-                } else {
-                    j = self;
-                    jend = self + 1u;
-                    on0 = false;
-                    on1 = false;
-                }
-            }
-        }
-        if (__any_sync(kFull, max(c0, c1) > kListCap2 - kSweepUnroll)) flush();
     }
     flush();
 
