@@ -40,6 +40,10 @@ k_bounds(const float4 *__restrict__ st, SimArgs sa, uint32_t *bounds, ug_grid_in
 }
 
 // ------------------------------------------------------------------ key + histogram
+// Each warp covers 2 x 32 consecutive rows (kKeyItems chunks), so that two
+// independent chains of loads and atomics are in flight per thread.
+constexpr int kKeyItems = 2;
+
 __global__ void __launch_bounds__(256)
 k_key(const float4 *__restrict__ st, SimArgs sa, const ug_grid_info *__restrict__ geo,
       Ctrl *ctrl, uint32_t *counts, uint32_t *__restrict__ key, uint32_t *__restrict__ rank,
@@ -54,33 +58,45 @@ k_key(const float4 *__restrict__ st, SimArgs sa, const ug_grid_info *__restrict_
         for (uint32_t s = gtid; s < sa.nsims; s += stride) geo_save[s] = geo[s];
     if (cta_failed(status)) return;
 
-    const uint32_t first = blockIdx.x * blockDim.x;
-    const uint32_t i = first + threadIdx.x;
-    const bool valid = i < sa.n;
-    bool uniform;
-    const uint32_t sim = cta_sim(sa, first, i, uniform);
-    uint32_t k = 0xffffffffu;
-    if (valid) {
-        const ug_grid_info g = geo[sim];
-        int bx, by, bz;
-        k = box_key(__ldg(st + i), g, bx, by, bz);
-    }
-    // rows arrive nearly sorted by box (the previous step's order), so equal
-    // keys mostly sit on consecutive lanes: each run of equal keys takes one
-    // atomic, and its lanes get consecutive provisional ranks
     const int lane = threadIdx.x & 31;
-    const uint32_t prevk = __shfl_up_sync(kFull, k, 1);
-    const bool head = lane == 0 || prevk != k;
-    const unsigned heads = __ballot_sync(kFull, head);
-    const int myhead = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
-    const unsigned after = lane == 31 ? 0u : heads & (0xffffffffu << (lane + 1));
-    const int nexthead = after ? __ffs(after) - 1 : 32;
-    uint32_t base = 0;
-    if (head && valid) base = atomicAdd(&counts[k], (uint32_t)(nexthead - lane));
-    base = __shfl_sync(kFull, base, myhead);
-    if (valid) {
-        rank[i] = base + (uint32_t)(lane - myhead);
-        key[i] = k;
+    const uint32_t first = blockIdx.x * blockDim.x * kKeyItems;
+    const uint32_t wbase = first + (threadIdx.x >> 5) * 32u * kKeyItems;
+    bool uniform;
+    const uint32_t csim = cta_sim_range(sa, first, blockDim.x * kKeyItems, uniform);
+    float4 p[kKeyItems];
+    uint32_t idx[kKeyItems];
+#pragma unroll
+    for (int it = 0; it < kKeyItems; ++it) {
+        idx[it] = wbase + 32u * it + lane;
+        p[it] = idx[it] < sa.n ? __ldg(st + idx[it]) : make_float4(0.f, 0.f, 0.f, 1.f);
+    }
+#pragma unroll
+    for (int it = 0; it < kKeyItems; ++it) {
+        const uint32_t i = idx[it];
+        const bool valid = i < sa.n;
+        uint32_t k = 0xffffffffu;
+        if (valid) {
+            const uint32_t sim = uniform ? csim : find_sim(sa, i);
+            const ug_grid_info g = geo[sim];
+            int bx, by, bz;
+            k = box_key(p[it], g, bx, by, bz);
+        }
+        // rows arrive nearly sorted by box (the previous step's order), so equal
+        // keys mostly sit on consecutive lanes: each run of equal keys takes one
+        // atomic, and its lanes get consecutive provisional ranks
+        const uint32_t prevk = __shfl_up_sync(kFull, k, 1);
+        const bool head = lane == 0 || prevk != k;
+        const unsigned heads = __ballot_sync(kFull, head);
+        const int myhead = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+        const unsigned after = lane == 31 ? 0u : heads & (0xffffffffu << (lane + 1));
+        const int nexthead = after ? __ffs(after) - 1 : 32;
+        uint32_t base = 0;
+        if (head && valid) base = atomicAdd(&counts[k], (uint32_t)(nexthead - lane));
+        base = __shfl_sync(kFull, base, myhead);
+        if (valid) {
+            rank[i] = base + (uint32_t)(lane - myhead);
+            key[i] = k;
+        }
     }
 }
 
@@ -215,8 +231,12 @@ k_place(const uint32_t *__restrict__ key, const uint32_t *__restrict__ rank,
         int32_t *status) {
     chain_begin();
     if (cta_failed(status)) return;
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) tmp[__ldg(start + __ldg(key + i)) + __ldg(rank + i)] = i;
+    const uint32_t i0 = blockIdx.x * blockDim.x * 2u + threadIdx.x, i1 = i0 + blockDim.x;
+    uint32_t k0 = 0, k1 = 0, r0 = 0, r1 = 0;
+    if (i0 < n) { k0 = __ldg(key + i0); r0 = __ldg(rank + i0); }
+    if (i1 < n) { k1 = __ldg(key + i1); r1 = __ldg(rank + i1); }
+    if (i0 < n) tmp[__ldg(start + k0) + r0] = i0;
+    if (i1 < n) tmp[__ldg(start + k1) + r1] = i1;
 }
 
 __global__ void __launch_bounds__(256)
@@ -227,18 +247,40 @@ k_canon(const uint32_t *__restrict__ tmp, const uint32_t *__restrict__ key,
         uint32_t *__restrict__ skey, int32_t *status) {
     chain_begin();
     if (cta_failed(status)) return;
-    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    const uint32_t id = __ldg(tmp + s);
-    const uint32_t k = __ldg(key + id);
-    const uint32_t b0 = __ldg(start + k), b1 = __ldg(start + k + 1);
-    uint32_t r = 0;
-    for (uint32_t t = b0; t < b1; ++t) r += __ldg(tmp + t) < id;
-    const uint32_t dest = b0 + r;
-    st_out[dest] = __ldg(st_in + id);
-    perm_out[dest] = perm_in ? __ldg(perm_in + id) : id;
-    if (sigma) sigma[dest] = id;
-    if (skey) skey[dest] = k;
+    // two slots per thread, their load chains interleaved
+    uint32_t sl[2], id[2], k[2], b0[2], b1[2];
+    sl[0] = blockIdx.x * blockDim.x * 2u + threadIdx.x;
+    sl[1] = sl[0] + blockDim.x;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) id[q] = sl[q] < n ? __ldg(tmp + sl[q]) : 0u;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) k[q] = sl[q] < n ? __ldg(key + id[q]) : 0u;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        b0[q] = sl[q] < n ? __ldg(start + k[q]) : 0u;
+        b1[q] = sl[q] < n ? __ldg(start + k[q] + 1) : 0u;
+    }
+    float4 row[2];
+    uint32_t pid[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        if (sl[q] < n) {
+            row[q] = __ldg(st_in + id[q]);
+            pid[q] = perm_in ? __ldg(perm_in + id[q]) : id[q];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        if (sl[q] >= n) continue;
+        // stable rank inside the box: rows of the box with a smaller input index
+        uint32_t r = 0;
+        for (uint32_t t = b0[q]; t < b1[q]; ++t) r += __ldg(tmp + t) < id[q];
+        const uint32_t dest = b0[q] + r;
+        st_out[dest] = row[q];
+        perm_out[dest] = pid[q];
+        if (sigma) sigma[dest] = id[q];
+        if (skey) skey[dest] = k[q];
+    }
 }
 
 // ------------------------------------------------------------------ launchers
@@ -257,7 +299,7 @@ void launch_bounds(const float4 *st, const SimArgs &sa, const Workspace &w, ug_g
 
 void launch_key(const float4 *st, const SimArgs &sa, const Workspace &w, const ug_grid_info *geo,
                 ug_grid_info *geo_save, int32_t *status, cudaStream_t s) {
-    launch_chained(k_key, blocks_for(sa.n, 256), 256, s, st, sa, geo, w.ctrl, w.counts, w.key,
+    launch_chained(k_key, blocks_for(sa.n, 256 * kKeyItems), 256, s, st, sa, geo, w.ctrl, w.counts, w.key,
                    w.rank, w.scan_status, w.ntiles, geo_save, status);
 }
 
@@ -271,13 +313,13 @@ void launch_scan(const Workspace &w, uint32_t *start, uint32_t max_boxes, int32_
 
 void launch_place(const Workspace &w, const uint32_t *start, uint32_t n, int32_t *status,
                   cudaStream_t s) {
-    launch_chained(k_place, blocks_for(n, 256), 256, s, w.key, w.rank, start, w.tmp, n, status);
+    launch_chained(k_place, blocks_for(n, 512), 256, s, w.key, w.rank, start, w.tmp, n, status);
 }
 
 void launch_canon(const Workspace &w, const uint32_t *start, const float4 *st_in,
                   const uint32_t *perm_in, float4 *st_sorted, uint32_t *perm_out, uint32_t *sigma,
                   uint32_t n, int32_t *status, cudaStream_t s, uint32_t *skey) {
-    launch_chained(k_canon, blocks_for(n, 256), 256, s, w.tmp, w.key, start, st_in, perm_in,
+    launch_chained(k_canon, blocks_for(n, 512), 256, s, w.tmp, w.key, start, st_in, perm_in,
                    st_sorted, perm_out, sigma, n, skey, status);
 }
 

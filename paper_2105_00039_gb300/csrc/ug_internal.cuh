@@ -114,6 +114,21 @@ __device__ __forceinline__ uint32_t cta_sim(const SimArgs &sa, uint32_t first, u
     return uniform ? s_sim[0] : find_sim(sa, min(i, sa.n - 1));
 }
 
+// Simulation shared by the `count` rows from `first` (when they share one):
+// every thread must call it; `uniform` tells whether they do.
+__device__ __forceinline__ uint32_t cta_sim_range(const SimArgs &sa, uint32_t first,
+                                                  uint32_t count, bool &uniform) {
+    __shared__ uint32_t s_sr[2];
+    if (sa.offset == nullptr || sa.nsims <= 1) { uniform = true; return 0; }
+    if (threadIdx.x == 0) {
+        s_sr[0] = find_sim(sa, min(first, sa.n - 1));
+        s_sr[1] = find_sim(sa, min(first + count, sa.n) - 1);
+    }
+    __syncthreads();
+    uniform = s_sr[0] == s_sr[1];
+    return s_sr[0];
+}
+
 // ------------------------------------------------------------------ ordered floats
 // Monotone map float -> uint32 (larger float, larger code); 0 is below every
 // float, so a zeroed word is the identity of atomicMax.
