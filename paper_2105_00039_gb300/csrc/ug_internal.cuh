@@ -17,7 +17,6 @@ constexpr int kScanTile = kScanThreads * kScanItems;   // boxes per look-back ti
 constexpr int kBoundsWords = 8;                         // per simulation, see bounds_*()
 constexpr int kBoundsCopiesSingle = 32;                 // spread atomics when nsims == 1
 constexpr uint32_t kSpinLimit = 1u << 22;               // bounded waits (x ~64 ns sleep)
-constexpr uint32_t kDenseOccupancy = 12;                // agents per box for the box-per-warp sweep
 
 // Control words living in the workspace (zeroed at the start of every call).
 struct Ctrl {
@@ -25,8 +24,7 @@ struct Ctrl {
     uint32_t done;          // CTAs finished (last-CTA pattern of the bounds reduction)
     uint32_t total_boxes;   // boxes of the current grid (all sims); 0 after an error
     uint32_t adj_done;      // last-CTA counter of the adjoint parameter reduction
-    uint32_t dense;         // 1: agents per box >= kDenseOccupancy (box-per-warp sweep)
-    uint32_t pad[3];
+    uint32_t pad[4];
 };
 
 // Which simulation owns which rows, and its constants.
@@ -549,7 +547,6 @@ __device__ __forceinline__ void finalize_grid(const SimArgs &sa, uint32_t *bound
         const unsigned long long total = s_carry;
         if (total > (unsigned long long)max_boxes) set_status(status, UG_EGRID_TOO_LARGE);
         ctrl->total_boxes = (s_bad || total > max_boxes) ? 0u : (uint32_t)total;
-        ctrl->dense = (unsigned long long)sa.n >= (unsigned long long)kDenseOccupancy * total ? 1u : 0u;
         ctrl->done = 0;
         __threadfence();
     }

@@ -42,85 +42,6 @@ __device__ __forceinline__ void add_contact(const float4 &me, const float4 &q, f
     ++a.np;
 }
 
-// Dense grids (many agents per box): every agent of a box has the same 9 runs,
-// so a warp takes whole boxes, lanes = the box's agents (32 at a time), and all
-// lanes read the same candidate row per iteration (a broadcast load): no
-// per-lane index arithmetic and no lockstep waste.  Boxes are dealt to warps
-// in a grid stride.  Each lane keeps the max of its agents' bounds codes.
-template <int MODE, int T>
-__device__ __forceinline__ void sweep_boxes(const float4 *__restrict__ st,
-                                            const uint32_t *__restrict__ start,
-                                            const ug_grid_info &g, const ug_params &P,
-                                            uint32_t nboxes, const SweepOut &out,
-                                            int32_t *status, WarpLists2 &w, uint32_t codes[8],
-                                            bool &any) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t nwarps = gridDim.x * (T / 32);
-    const uint32_t gw = blockIdx.x * (T / 32) + (threadIdx.x >> 5);
-    const float m2 = 2.0f * P.contact_margin;
-    const int dx = g.dims[0], plane = g.dims[0] * g.dims[1];
-    const float4 far = make_float4(1e30f, 1e30f, 1e30f, 1.0f);
-    for (uint32_t b = gw; b < nboxes; b += nwarps) {
-        const uint32_t a0 = __ldg(start + b), a1 = __ldg(start + b + 1);
-        if (a1 == a0) continue;          // only boxes with agents (always interior)
-        uint32_t rb = 0, re = 0;
-        if (lane < 9) {
-            const uint32_t kb = (uint32_t)((int)b + (lane / 3 - 1) * plane + (lane % 3 - 1) * dx);
-            rb = __ldg(start + kb - 1);
-            re = __ldg(start + kb + 2);
-        }
-        for (uint32_t c0 = a0; c0 < a1; c0 += 32) {
-            const uint32_t i = c0 + lane;
-            const bool valid = i < a1;
-            const float4 me = valid ? __ldg(st + i) : far;
-            const FilterRow f = make_filter_row(me, m2);
-            const bool exact_diffs = __all_sync(kFull, !valid || far_from_origin(me, g.edge));
-            Accum a{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u};
-            int cnt = 0;
-            auto flush = [&]() {
-                const int m = (int)__reduce_max_sync(kFull, (unsigned)cnt);
-                for (int k = 0; k < m; ++k)
-                    if (k < cnt) add_contact(me, __ldg(st + w.lst[0][k][lane]), m2, exact_diffs, P, a);
-                cnt = 0;
-            };
-#pragma unroll 1
-            for (int r = 0; r < 9; ++r) {
-                const uint32_t jb = __shfl_sync(kFull, rb, r), je = __shfl_sync(kFull, re, r);
-                for (uint32_t j = jb; j < je; j += 4) {
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const uint32_t jj = j + u;
-                        const float4 q = __ldg(st + min(jj, je - 1u));
-                        if ((jj < je) & valid & (jj != i) & prefilter(q, f)) {
-                            w.lst[0][cnt][lane] = jj;
-                            ++cnt;
-                        }
-                    }
-                    if (__any_sync(kFull, cnt > kListCap - 4)) flush();
-                }
-            }
-            flush();
-            if (!valid) continue;
-            const float3 F = make_float3(a.sx + a.cx, a.sy + a.cy, a.sz + a.cz);
-            if (MODE == kSweepForce) {
-                out.force[i] = make_float4(F.x, F.y, F.z, (float)a.np);
-                continue;
-            }
-            bool mv, cp;
-            const float3 u = displacement(F.x, F.y, F.z, me.w, P, &mv, &cp);
-            const float4 nw = make_float4(me.x + u.x, me.y + u.y, me.z + u.z, me.w);
-            out.state_out[i] = nw;
-            if (out.force) out.force[i] = make_float4(F.x, F.y, F.z, (mv ? 1.f : 0.f) + (cp ? 2.f : 0.f));
-            if (!row_ok(nw)) set_status(status, UG_EBADSTATE);
-            uint32_t c[8];
-            bounds_codes(nw, true, c);
-#pragma unroll
-            for (int k = 0; k < 8; ++k) codes[k] = max(codes[k], c[k]);
-            any = true;
-        }
-    }
-}
-
 template <int MODE, int T>
 __global__ void __launch_bounds__(T, 8)
 k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
@@ -136,16 +57,6 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     const bool v0 = i0 < n, v1 = i1 < n;
     const ug_params P = sa.pval;
     const ug_grid_info g = geo[0];
-    if (MODE == kSweepStep && *(volatile const uint32_t *)&out.ctrl->dense) {
-        uint32_t codes[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-        bool any = false;
-        sweep_boxes<MODE, T>(st, start, g, P, *(volatile const uint32_t *)&out.ctrl->total_boxes,
-                             out, status, w, codes, any);
-        accumulate_bounds_codes(sa, codes, any, 0u, true, out.bounds);
-        if (elect_last_cta(&out.ctrl->done))
-            finalize_grid(sa, out.bounds, out.geo_next, out.ctrl, out.max_boxes, status);
-        return;
-    }
     const float m2 = 2.0f * P.contact_margin;
     const float4 far = make_float4(1e30f, 1e30f, 1e30f, 1.0f);
     const float4 me0 = v0 ? __ldg(st + i0) : far;
