@@ -442,3 +442,31 @@ def test_density_sweep_4m_sampled(U, nbar):
     x = _gpu(st)
     nb = _sampled_check(U, x, O.Params(max_disp=0.0), U.Params(max_disp=0.0), nsample=1500)
     assert 0.6 * nbar < nb < 1.2 * nbar
+
+
+def test_dense_grid_step(U):
+    """A dense population (about 24 agents per box, ~60 neighbours per agent):
+    one fused step against the oracle, and three steps bit for bit against the
+    one-agent-per-lane sweep of the batched entry."""
+    st = P.density_cube(20000, 60.0, seed=31)
+    prm = O.Params()
+    out, perm = _run_steps(U, st, U.Params(), 1)
+    newg = by_id(out.astype(np.float64), perm)
+    ref = O.step(st, prm)
+    flips = adherence_flips(ref["Fn"], ref["S"], prm.adherence)
+    scale = ref["S"] / O.mass(st[:, 3].astype(np.float64), prm.as64())
+    dp = np.abs(newg[:, :3] - ref["state"][:, :3])
+    ok = dp <= ulp32(newg[:, :3]) + TOL_STEP * np.maximum(np.linalg.norm(ref["u"], axis=1),
+                                                          scale)[:, None]
+    assert ok[~flips].all()
+    # three steps: two agents per lane (plain) == one agent per lane (batched, 1 simulation)
+    a, pa = _run_steps(U, st, U.Params(), 3)
+    x = _gpu(st)
+    t = U.ug_tuning()
+    t.agents_per_lane, t.sweep_block = 1, 128
+    sp = U.Stepper(len(st), U.estimate_max_boxes(x, 0.0, slack=2.0), x.device, nsims=1)
+    pb = U.iota(len(st), x.device)
+    sp.step_batched(x, pb, torch.tensor([0, len(st)], dtype=torch.int32, device=DEV),
+                    U.Params().as_tensor(DEV)[None], 3, t)
+    sp.check("batched-1")
+    assert np.array_equal(a, x.cpu().numpy()) and np.array_equal(pa, pb.cpu().numpy())
