@@ -5,8 +5,8 @@
 // of the 9 neighbour rows the two agents' candidate runs merge into one run,
 // boxes [bx(2l) - 1, bx(2l+1) + 1]: every candidate row is loaded once and
 // tested against both agents, which halves the per-candidate index, load and
-// loop work of the one-agent-per-lane sweep.  A lane whose two agents lie in
-// different rows walks the two 9-run sets one after the other.  Runs are
+// loop work of the one-agent-per-lane sweep.  A lane whose two agents lie too
+// far apart in box order to merge walks the two 9-run sets one after the other.  Runs are
 // walked in warp lockstep (trip count = the warp's longest run) with clamped
 // indices and masks, candidates that pass the packed float32 pre-filter go to
 // per-agent lists, and the exact float-float contact test and Eq. 1 run in
@@ -42,6 +42,21 @@ __device__ __forceinline__ void add_contact(const float4 &me, const float4 &q, f
     ++a.np;
 }
 
+// The two agents' windows merge into one run per neighbour row, boxes
+// [k0 - 1, k1 + 1] shifted by the row's offset, when no two of the 9 merged
+// runs can overlap: the 9 offsets are at least one x-row (dims_x boxes) apart,
+// so runs of k1 - k0 + 3 boxes stay disjoint while k1 - k0 <= dims_x - 3.
+// That holds for two agents of one x-row and for the usual pair that straddles
+// a row end (the boxes between them are the two empty padding boxes).  As the
+// runs are disjoint, the extra boxes a merged run covers lie outside both
+// agents' 27-box neighbourhoods, so no contact is found (or counted twice)
+// there.  The order in which an agent meets
+// its contacts is the same merged or split: ascending within each run, runs in
+// the same order.
+__device__ __forceinline__ bool mergeable(uint32_t k0, uint32_t k1, uint32_t dx) {
+    return k1 >= k0 && k1 - k0 + 3u <= dx;
+}
+
 template <int MODE, int T>
 __global__ void __launch_bounds__(T, 8)
 k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
@@ -70,7 +85,7 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     }
     const uint32_t dx = (uint32_t)g.dims[0];
     const int plane = g.dims[0] * g.dims[1];
-    const bool split = v1 && ((k0 - g.box_base) / dx != (k1 - g.box_base) / dx);
+    const bool split = v1 && !mergeable(k0, k1, dx);
     const bool exact_diffs =
         __all_sync(kFull, (!v0 || far_from_origin(me0, g.edge)) && (!v1 || far_from_origin(me1, g.edge)));
     const FilterRow f0 = make_filter_row(me0, m2), f1 = make_filter_row(me1, m2);
@@ -202,8 +217,7 @@ k_sweep2m(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
         k1 = k0;
         if (v1) k1 = skey ? __ldg(skey + i1) : box_key(me1, g1, bx, by, bz);
     }
-    const bool split = v1 && (s1 != s0 || (k0 - g0.box_base) / (uint32_t)g0.dims[0] !=
-                                             (k1 - g0.box_base) / (uint32_t)g0.dims[0]);
+    const bool split = v1 && (s1 != s0 || !mergeable(k0, k1, (uint32_t)g0.dims[0]));
     const bool exact_diffs = __all_sync(kFull, (!v0 || far_from_origin(me0, g0.edge)) &&
                                                    (!v1 || far_from_origin(me1, g1.edge)));
     const FilterRow f0 = make_filter_row(me0, m20), f1 = make_filter_row(me1, m21);
