@@ -24,7 +24,7 @@
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call is
  *     asynchronous: the return value reports argument and launch errors only.
  *     Errors found on the device (bad input values, grid too large, a list
- *     overflow, a spin-wait timeout) are written to `*status` (a device int32
+ *     overflow) are written to `*status` (a device int32
  *     the caller zeroes before the first call; the first error wins and later
  *     kernels of the same call become no-ops).  Read it after synchronising.
  *   - Calls on different streams must use different workspaces.  The library
@@ -49,7 +49,7 @@ extern "C" {
 #define UG_EGRID_TOO_LARGE (-3) /* device: the grid needs more than max_boxes boxes */
 #define UG_ECAPACITY       (-4) /* device: a per-agent output list was too short */
 #define UG_EWORKSPACE      (-5) /* ws_bytes smaller than the *_workspace_bytes figure */
-#define UG_ETIMEOUT        (-6) /* device: a bounded spin-wait gave up (should never happen) */
+#define UG_ETIMEOUT        (-6) /* reserved: no kernel of this library waits on another */
 #define UG_ECUDA           (-7) /* a CUDA runtime call failed (launch, memset, copy) */
 
 /* Human-readable text for a status code (static storage, never NULL). */
@@ -57,12 +57,6 @@ const char *ug_strerror(int status);
 
 /* Library ABI version (major * 10000 + minor * 100 + patch). */
 int ug_version(void);
-
-/* Fault injection for tests: set the process-wide bound on the polls of the
- * grid scan's bounded waits (default 4194304) and return the previous bound.
- * With 0, a scan tile that finds a predecessor not yet published gives up at
- * once and reports UG_ETIMEOUT instead of waiting; nothing ever hangs. */
-uint32_t ug_debug_spin_limit(uint32_t limit);
 
 /* ------------------------------------------------------------------ types */
 

@@ -27,8 +27,8 @@ int device_sm_count() {
 
 static uint32_t bounds_copies(uint32_t nsims) { return nsims == 1 ? kBoundsCopiesSingle : 1u; }
 
-// Layout (base may be null to size only).  The first three regions (ctrl,
-// counts, bounds) are contiguous and are the only ones that need zeroing.
+// Layout (base may be null to size only).  The first four regions (ctrl, tile
+// sums, counts, bounds) are contiguous and are the only ones that need zeroing.
 size_t layout_workspace(void *base, uint32_t n, uint32_t nsims, uint32_t max_boxes, Workspace *w) {
     size_t off = 0;
     char *b = static_cast<char *>(base);
@@ -38,6 +38,8 @@ size_t layout_workspace(void *base, uint32_t n, uint32_t nsims, uint32_t max_box
         return p;
     };
     w->ctrl = reinterpret_cast<Ctrl *>(take(sizeof(Ctrl)));
+    w->ntiles = std::max<uint32_t>(1u, (uint32_t)(((size_t)max_boxes + kScanTile - 1) / kScanTile));
+    w->tile_sum = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (size_t)w->ntiles));
     w->counts = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (size_t)max_boxes));
     w->bounds = reinterpret_cast<uint32_t *>(
         take(sizeof(uint32_t) * kBoundsWords * (size_t)bounds_copies(nsims) * nsims));
@@ -49,8 +51,6 @@ size_t layout_workspace(void *base, uint32_t n, uint32_t nsims, uint32_t max_box
     w->sorted = reinterpret_cast<float4 *>(take(sizeof(float4) * (size_t)n));
     w->perm2 = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (size_t)n));
     w->geo = reinterpret_cast<ug_grid_info *>(take(sizeof(ug_grid_info) * (size_t)nsims));
-    w->ntiles = std::max<uint32_t>(1u, (uint32_t)(((size_t)max_boxes + kScanTile - 1) / kScanTile));
-    w->scan_status = reinterpret_cast<unsigned long long *>(take(8 * (size_t)w->ntiles));
     w->bytes = off;
     (void)zero_end;
     return off;
@@ -146,15 +146,13 @@ const char *ug_strerror(int status) {
     case UG_EGRID_TOO_LARGE: return "grid needs more boxes than max_boxes";
     case UG_ECAPACITY: return "per-agent output list too short";
     case UG_EWORKSPACE: return "workspace too small";
-    case UG_ETIMEOUT: return "bounded device wait timed out";
+    case UG_ETIMEOUT: return "reserved (device wait timed out)";
     case UG_ECUDA: return "CUDA runtime error";
     default: return "unknown status";
     }
 }
 
 int ug_version(void) { return 10000; }
-
-uint32_t ug_debug_spin_limit(uint32_t limit) { return set_spin_limit(limit); }
 
 size_t ug_workspace_bytes(uint32_t n, uint32_t nsims, uint32_t max_boxes) {
     Workspace w;

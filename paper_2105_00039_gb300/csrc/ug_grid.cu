@@ -9,15 +9,15 @@
 //   k_bounds  (first step only; later steps get it from the sweep epilogue)
 //             per-simulation min/max corner and max diameter -> grid geometry
 //   k_key     box key of every row + warp-aggregated atomic histogram; the
-//             atomic's return value is a provisional rank inside the box
-//   k_scan    single-pass exclusive scan of the box counts with a warp-wide
-//             decoupled look-back (bounded spins), also re-zeroing the counts
-//   k_place   row index -> provisional slot
+//             atomic's return value is a provisional rank inside the box; the
+//             rows of every scan tile (8192 boxes) are summed on the side
+//   k_scan    exclusive scan of the box counts, one CTA per tile, whose prefix
+//             is the sum of the earlier tiles' row counts (no inter-CTA wait),
+//             also re-zeroing the counts
+//   k_place   row index -> provisional slot; re-zeroes the tile sums
 //   k_canon   stable order inside each box (rank = rows of the box with a
 //             smaller input index), gathering rows and ids into that slot
 #include <cuda_runtime.h>
-
-#include <atomic>
 
 #include "ug_internal.cuh"
 
@@ -46,14 +46,11 @@ constexpr int kKeyItems = 2;
 
 __global__ void __launch_bounds__(256)
 k_key(const float4 *__restrict__ st, SimArgs sa, const ug_grid_info *__restrict__ geo,
-      Ctrl *ctrl, uint32_t *counts, uint32_t *__restrict__ key, uint32_t *__restrict__ rank,
-      unsigned long long *scan_status, uint32_t ntiles, ug_grid_info *geo_save,
-      int32_t *status) {
+      uint32_t *counts, uint32_t *tile_sum, uint32_t *__restrict__ key,
+      uint32_t *__restrict__ rank, ug_grid_info *geo_save, int32_t *status) {
     chain_begin();
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t t = gtid; t < ntiles; t += stride) scan_status[t] = 0ull;
-    if (gtid == 0) ctrl->scan_ticket = 0u;
     if (geo_save)
         for (uint32_t s = gtid; s < sa.nsims; s += stride) geo_save[s] = geo[s];
     if (cta_failed(status)) return;
@@ -92,6 +89,17 @@ k_key(const float4 *__restrict__ st, SimArgs sa, const ug_grid_info *__restrict_
         const int nexthead = after ? __ffs(after) - 1 : 32;
         uint32_t base = 0;
         if (head && valid) base = atomicAdd(&counts[k], (uint32_t)(nexthead - lane));
+        // rows per scan tile: one atomic per warp when its rows share a tile
+        const unsigned vmask = __ballot_sync(kFull, valid);
+        if (vmask) {
+            const uint32_t tl = k >> kScanTileShift;
+            const uint32_t tl0 = __shfl_sync(kFull, tl, __ffs(vmask) - 1);
+            if (__all_sync(kFull, !valid || tl == tl0)) {
+                if (lane == __ffs(vmask) - 1) atomicAdd(&tile_sum[tl0], (uint32_t)__popc(vmask));
+            } else if (valid) {
+                atomicAdd(&tile_sum[tl], 1u);
+            }
+        }
         base = __shfl_sync(kFull, base, myhead);
         if (valid) {
             rank[i] = base + (uint32_t)(lane - myhead);
@@ -100,60 +108,29 @@ k_key(const float4 *__restrict__ st, SimArgs sa, const ug_grid_info *__restrict_
     }
 }
 
-// ------------------------------------------------------------------ look-back scan
-// Tile status word: flag << 32 | value; flag 0 = not ready, 1 = tile sum only,
-// 2 = inclusive prefix of everything up to and including the tile.
-__device__ __forceinline__ void publish(unsigned long long *st, uint32_t t, uint32_t flag,
-                                        uint32_t val) {
-    *(volatile unsigned long long *)(st + t) = ((unsigned long long)flag << 32) | val;
-}
-
-// Exclusive prefix of tile t from its predecessors' status words, read by one
-// warp 32 tiles at a time (lane l looks at tile t-1-l): sum tile aggregates
-// back to the nearest tile that already knows its inclusive prefix.  Waits are
-// bounded; on timeout the error is recorded and the partial sum returned so
-// that successors finish too.
-__device__ uint32_t look_back_warp(unsigned long long *st, uint32_t t, uint32_t spin_limit,
-                                   int32_t *status) {
-    const int lane = threadIdx.x & 31;
-    uint32_t excl = 0;
-    int j = (int)t - 1 - lane;
-    uint32_t spins = 0;
-    for (;;) {
-        const unsigned long long w =
-            j >= 0 ? *(volatile unsigned long long *)(st + j) : (2ull << 32);
-        const uint32_t flag = (uint32_t)(w >> 32);
-        if (__any_sync(kFull, flag == 0u)) {
-            if (++spins > spin_limit || peek_status(status) != 0) {
-                set_status(status, UG_ETIMEOUT);
-                return excl;
-            }
-            __nanosleep(32);
-            continue;
-        }
-        const unsigned pmask = __ballot_sync(kFull, flag == 2u);
-        const int first = pmask ? __ffs(pmask) - 1 : 31;
-        excl += __reduce_add_sync(kFull, lane <= first ? (uint32_t)w : 0u);
-        if (pmask) return excl;
-        j -= 32;
-    }
-}
-
+// ------------------------------------------------------------------ tile scan
+// CTA t scans boxes [t * kScanTile, (t + 1) * kScanTile).  Its exclusive
+// prefix, the rows in all earlier boxes, is the sum of the earlier tiles' row
+// counts that k_key accumulated, so no CTA waits on another.
 __global__ void __launch_bounds__(kScanThreads)
-k_scan(uint32_t *__restrict__ counts, uint32_t *__restrict__ start, Ctrl *ctrl,
-       unsigned long long *tstat, uint32_t spin_limit, int32_t *status) {
-    __shared__ uint32_t s_tile, s_prefix;
+k_scan(uint32_t *__restrict__ counts, uint32_t *__restrict__ start, const Ctrl *ctrl,
+       const uint32_t *__restrict__ tile_sum, int32_t *status) {
     __shared__ uint32_t s_warp[kScanThreads / 32];
+    __shared__ uint32_t s_pre[kScanThreads / 32];
     chain_begin();
     if (cta_failed(status)) return;
-    const uint32_t B = *(volatile uint32_t *)&ctrl->total_boxes;
+    const uint32_t B = *(volatile const uint32_t *)&ctrl->total_boxes;
     const uint32_t ntiles = (B + kScanTile - 1) / kScanTile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(&ctrl->scan_ticket, 1u);
-        __syncthreads();
-        const uint32_t t = s_tile;
-        if (t >= ntiles) break;
+    const uint32_t t = blockIdx.x;
+    if (t >= ntiles) return;
+    {
+        uint32_t pre = 0;
+        for (uint32_t u = threadIdx.x; u < t; u += kScanThreads) pre += __ldg(tile_sum + u);
+        pre = __reduce_add_sync(kFull, pre);
+        if (lane == 0) s_pre[warp] = pre;
+    }
+    {
         const uint32_t base = t * kScanTile + threadIdx.x * kScanItems;
         uint32_t v[kScanItems];
         if (base + kScanItems <= B) {
@@ -185,19 +162,10 @@ k_scan(uint32_t *__restrict__ counts, uint32_t *__restrict__ start, Ctrl *ctrl,
             if (w < warp) wbase += x;
             tile_total += x;
         }
-        if (warp == 0) {
-            uint32_t excl = 0;
-            if (t == 0) {
-                if (lane == 0) publish(tstat, t, 2u, tile_total);
-            } else {
-                if (lane == 0) publish(tstat, t, 1u, tile_total);
-                excl = look_back_warp(tstat, t, spin_limit, status);
-                if (lane == 0) publish(tstat, t, 2u, excl + tile_total);
-            }
-            if (lane == 0) s_prefix = excl;
-        }
-        __syncthreads();
-        uint32_t run = s_prefix + wbase + inc - tsum;
+        uint32_t excl = 0;
+#pragma unroll
+        for (int w = 0; w < kScanThreads / 32; ++w) excl += s_pre[w];
+        uint32_t run = excl + wbase + inc - tsum;
         if (base + kScanItems <= B) {
 #pragma unroll
             for (int q = 0; q < kScanItems / 4; ++q) {
@@ -219,8 +187,7 @@ k_scan(uint32_t *__restrict__ counts, uint32_t *__restrict__ start, Ctrl *ctrl,
                 run += v[k];
             }
         }
-        if (t == ntiles - 1 && threadIdx.x == 0) start[B] = s_prefix + tile_total;
-        __syncthreads();
+        if (t == ntiles - 1 && threadIdx.x == 0) start[B] = excl + tile_total;
     }
 }
 
@@ -228,8 +195,11 @@ k_scan(uint32_t *__restrict__ counts, uint32_t *__restrict__ start, Ctrl *ctrl,
 __global__ void __launch_bounds__(256)
 k_place(const uint32_t *__restrict__ key, const uint32_t *__restrict__ rank,
         const uint32_t *__restrict__ start, uint32_t *__restrict__ tmp, uint32_t n,
-        int32_t *status) {
+        uint32_t *__restrict__ tile_sum, uint32_t ntiles, int32_t *status) {
     chain_begin();
+    // the scan has consumed the tile sums: clear them for the next rebuild
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x)
+        tile_sum[t] = 0u;
     if (cta_failed(status)) return;
     const uint32_t i0 = blockIdx.x * blockDim.x * 2u + threadIdx.x, i1 = i0 + blockDim.x;
     uint32_t k0 = 0, k1 = 0, r0 = 0, r1 = 0;
@@ -286,11 +256,6 @@ k_canon(const uint32_t *__restrict__ tmp, const uint32_t *__restrict__ key,
 // ------------------------------------------------------------------ launchers
 static inline unsigned blocks_for(uint32_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-// Bound on the look-back polls of the scan, process-wide (see ug_debug_spin_limit).
-static std::atomic<uint32_t> g_spin_limit{kSpinLimit};
-uint32_t spin_limit() { return g_spin_limit.load(std::memory_order_relaxed); }
-uint32_t set_spin_limit(uint32_t v) { return g_spin_limit.exchange(v); }
-
 void launch_bounds(const float4 *st, const SimArgs &sa, const Workspace &w, ug_grid_info *geo,
                    uint32_t max_boxes, int32_t *status, cudaStream_t s) {
     launch_chained(k_bounds, blocks_for(sa.n, 256), 256, s, st, sa, w.bounds, geo, w.ctrl,
@@ -299,21 +264,21 @@ void launch_bounds(const float4 *st, const SimArgs &sa, const Workspace &w, ug_g
 
 void launch_key(const float4 *st, const SimArgs &sa, const Workspace &w, const ug_grid_info *geo,
                 ug_grid_info *geo_save, int32_t *status, cudaStream_t s) {
-    launch_chained(k_key, blocks_for(sa.n, 256 * kKeyItems), 256, s, st, sa, geo, w.ctrl, w.counts, w.key,
-                   w.rank, w.scan_status, w.ntiles, geo_save, status);
+    launch_chained(k_key, blocks_for(sa.n, 256 * kKeyItems), 256, s, st, sa, geo, w.counts, w.tile_sum,
+                   w.key, w.rank, geo_save, status);
 }
 
 void launch_scan(const Workspace &w, uint32_t *start, uint32_t max_boxes, int32_t *status,
                  cudaStream_t s) {
     (void)max_boxes;
-    const unsigned grid = (unsigned)min((int)w.ntiles, 2 * device_sm_count());
-    launch_chained(k_scan, grid > 0 ? grid : 1u, (unsigned)kScanThreads, s, w.counts, start, w.ctrl,
-                   w.scan_status, spin_limit(), status);
+    launch_chained(k_scan, w.ntiles, (unsigned)kScanThreads, s, w.counts, start,
+                   (const Ctrl *)w.ctrl, (const uint32_t *)w.tile_sum, status);
 }
 
 void launch_place(const Workspace &w, const uint32_t *start, uint32_t n, int32_t *status,
                   cudaStream_t s) {
-    launch_chained(k_place, blocks_for(n, 512), 256, s, w.key, w.rank, start, w.tmp, n, status);
+    launch_chained(k_place, blocks_for(n, 512), 256, s, w.key, w.rank, start, w.tmp, n, w.tile_sum,
+                   w.ntiles, status);
 }
 
 void launch_canon(const Workspace &w, const uint32_t *start, const float4 *st_in,

@@ -13,14 +13,15 @@ namespace ug {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kScanThreads = 512;
 constexpr int kScanItems = 16;
-constexpr int kScanTile = kScanThreads * kScanItems;   // boxes per look-back tile
+constexpr int kScanTile = kScanThreads * kScanItems;   // boxes per scan tile (a power of 2)
+constexpr int kScanTileShift = 13;
+static_assert(kScanTile == 1 << kScanTileShift, "scan tile must be 2^kScanTileShift boxes");
 constexpr int kBoundsWords = 8;                         // per simulation, see bounds_*()
 constexpr int kBoundsCopiesSingle = 32;                 // spread atomics when nsims == 1
-constexpr uint32_t kSpinLimit = 1u << 22;               // bounded waits (x ~64 ns sleep)
 
 // Control words living in the workspace (zeroed at the start of every call).
 struct Ctrl {
-    uint32_t scan_ticket;   // dynamic tile index of the look-back scan
+    uint32_t spare;
     uint32_t done;          // CTAs finished (last-CTA pattern of the bounds reduction)
     uint32_t total_boxes;   // boxes of the current grid (all sims); 0 after an error
     uint32_t adj_done;      // last-CTA counter of the adjoint parameter reduction
@@ -577,7 +578,7 @@ struct Workspace {
     uint32_t *perm2;       // [n]
     ug_grid_info *geo;     // [nsims]
     uint32_t *bounds;      // [copies * nsims * 8]
-    unsigned long long *scan_status;   // [ntiles]
+    uint32_t *tile_sum;    // [ntiles]        rows per scan tile, zero between steps
     Ctrl *ctrl;
     uint32_t ntiles;
     size_t bytes;
@@ -588,8 +589,6 @@ int device_sm_count();
 
 // ------------------------------------------------------------------ launchers
 // Grid build pieces (ug_grid.cu).  All asynchronous on `s`.
-uint32_t spin_limit();
-uint32_t set_spin_limit(uint32_t v);
 void launch_bounds(const float4 *st, const SimArgs &sa, const Workspace &w, ug_grid_info *geo,
                    uint32_t max_boxes, int32_t *status, cudaStream_t s);
 void launch_key(const float4 *st, const SimArgs &sa, const Workspace &w, const ug_grid_info *geo,

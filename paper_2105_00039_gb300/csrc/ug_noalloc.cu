@@ -28,14 +28,14 @@ constexpr uint32_t kNoAllocMaxBoxes = 1u << 20;    // 1,048,576 grid boxes
 constexpr size_t kAlign = 256;
 constexpr size_t up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 constexpr size_t kNoAllocTiles = (kNoAllocMaxBoxes + ug::kScanTile - 1) / ug::kScanTile;
-// ctrl | counts | bounds (these three are zeroed per call) | key | rank | tmp | tile status
-constexpr size_t kOffCounts = up(sizeof(ug::Ctrl));
+// ctrl | tile sums | counts | bounds (these four are zeroed per call) | key | rank | tmp
+constexpr size_t kOffTiles = up(sizeof(ug::Ctrl));
+constexpr size_t kOffCounts = kOffTiles + up(4ull * kNoAllocTiles);
 constexpr size_t kOffBounds = kOffCounts + up(4ull * kNoAllocMaxBoxes);
 constexpr size_t kOffKey = kOffBounds + up(4ull * ug::kBoundsWords * ug::kBoundsCopiesSingle);
 constexpr size_t kOffRank = kOffKey + up(4ull * kNoAllocMaxAgents);
 constexpr size_t kOffTmp = kOffRank + up(4ull * kNoAllocMaxAgents);
-constexpr size_t kOffTiles = kOffTmp + up(4ull * kNoAllocMaxAgents);
-constexpr size_t kScratchBytes = kOffTiles + up(8ull * kNoAllocTiles);
+constexpr size_t kScratchBytes = kOffTmp + up(4ull * kNoAllocMaxAgents);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -84,12 +84,12 @@ extern "C" int ug_grid_build_noalloc(const float *state_in, const uint32_t *perm
     w.key = reinterpret_cast<uint32_t *>(b + kOffKey);
     w.rank = reinterpret_cast<uint32_t *>(b + kOffRank);
     w.tmp = reinterpret_cast<uint32_t *>(b + kOffTmp);
-    w.scan_status = reinterpret_cast<unsigned long long *>(b + kOffTiles);
+    w.tile_sum = reinterpret_cast<uint32_t *>(b + kOffTiles);
     w.ntiles = (max_boxes + kScanTile - 1) / kScanTile;
     w.bytes = kScratchBytes;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // counts must start at zero; the previous call left them zero unless it
-    // failed part-way, so clear them with the control words and bounds
+    // tile sums and counts must start at zero; the previous call left them zero
+    // unless it failed part-way, so clear them with the control words and bounds
     if (cudaMemsetAsync(b, 0, kOffBounds + 4ull * kBoundsWords * kBoundsCopiesSingle, s) != cudaSuccess)
         return UG_ECUDA;
     SimArgs sa{};

@@ -29,7 +29,7 @@ EXPORTED = ("ug_strerror", "ug_version", "ug_workspace_bytes", "ug_grid_build",
             "ug_step_traced",
             "ug_step_batched", "ug_tune_batched", "ug_backward_workspace_bytes",
             "ug_step_backward", "ug_iota", "ug_scatter_rows", "ug_gather_rows",
-            "ug_grid_build_noalloc", "ug_debug_spin_limit")
+            "ug_grid_build_noalloc")
 
 
 class UgError(RuntimeError):
@@ -82,7 +82,6 @@ _U32 = ctypes.c_uint32
 _SIG = {
     "ug_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "ug_version": (ctypes.c_int, []),
-    "ug_debug_spin_limit": (ctypes.c_uint32, [ctypes.c_uint32]),
     "ug_workspace_bytes": (ctypes.c_size_t, [_U32, _U32, _U32]),
     "ug_grid_build": (ctypes.c_int, [_P, _P, _U32, ctypes.c_float, _P, _P, _P, _U32, _P, _P,
                                      ctypes.c_size_t, _P, _P]),

@@ -65,6 +65,19 @@ def test_grid_build_with_input_ids(U):
     assert np.array_equal(perm.cpu().numpy(), ids[g["perm"]])
 
 
+def test_grid_build_exact_many_scan_tiles(U):
+    """2^21 agents on 140^3 = 2.7M boxes: 335 scan tiles of 8192 boxes, each
+    taking its prefix from the earlier tiles' row counts."""
+    st = P.density_cube(1 << 21, 2.0, seed=21)
+    g = O.grid(st)
+    assert g["nboxes"] > 300 * 8192
+    srt, perm, start, info, _ = U.grid_build(_gpu(st), max_boxes=g["nboxes"] + 7)
+    assert U.grid_info_from_bytes(info)["nboxes"] == g["nboxes"]
+    assert np.array_equal(start.cpu().numpy()[: g["nboxes"] + 1], g["start"])
+    assert np.array_equal(perm.cpu().numpy(), g["perm"])
+    assert np.array_equal(srt.cpu().numpy(), st[g["perm"]])
+
+
 # ------------------------------------------------------------------ pairs
 @pytest.mark.parametrize("name", list(workloads()))
 def test_contact_pairs_exact(U, name):
