@@ -95,9 +95,10 @@ k_key(const float4 *__restrict__ st, SimArgs sa, const ug_grid_info *__restrict_
             const uint32_t tl = k >> kScanTileShift;
             const uint32_t tl0 = __shfl_sync(kFull, tl, __ffs(vmask) - 1);
             if (__all_sync(kFull, !valid || tl == tl0)) {
-                if (lane == __ffs(vmask) - 1) atomicAdd(&tile_sum[tl0], (uint32_t)__popc(vmask));
+                if (lane == __ffs(vmask) - 1)
+                    atomicAdd(&tile_sum[tl0 * kTileSumStride], (uint32_t)__popc(vmask));
             } else if (valid) {
-                atomicAdd(&tile_sum[tl], 1u);
+                atomicAdd(&tile_sum[tl * kTileSumStride], 1u);
             }
         }
         base = __shfl_sync(kFull, base, myhead);
@@ -126,7 +127,8 @@ k_scan(uint32_t *__restrict__ counts, uint32_t *__restrict__ start, const Ctrl *
     if (t >= ntiles) return;
     {
         uint32_t pre = 0;
-        for (uint32_t u = threadIdx.x; u < t; u += kScanThreads) pre += __ldg(tile_sum + u);
+        for (uint32_t u = threadIdx.x; u < t; u += kScanThreads)
+            pre += __ldg(tile_sum + (size_t)u * kTileSumStride);
         pre = __reduce_add_sync(kFull, pre);
         if (lane == 0) s_pre[warp] = pre;
     }
@@ -199,7 +201,7 @@ k_place(const uint32_t *__restrict__ key, const uint32_t *__restrict__ rank,
     chain_begin();
     // the scan has consumed the tile sums: clear them for the next rebuild
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x)
-        tile_sum[t] = 0u;
+        tile_sum[(size_t)t * kTileSumStride] = 0u;
     if (cta_failed(status)) return;
     const uint32_t i0 = blockIdx.x * blockDim.x * 2u + threadIdx.x, i1 = i0 + blockDim.x;
     uint32_t k0 = 0, k1 = 0, r0 = 0, r1 = 0;

@@ -16,6 +16,9 @@ constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;   // boxes per scan tile (a power of 2)
 constexpr int kScanTileShift = 13;
 static_assert(kScanTile == 1 << kScanTileShift, "scan tile must be 2^kScanTileShift boxes");
+// Each tile's row count sits on its own 128-byte line (tile_sum[t * kTileSumStride]),
+// so that the histogram's per-warp atomics spread over L2 slices.
+constexpr uint32_t kTileSumStride = 32;
 constexpr int kBoundsWords = 8;                         // per simulation, see bounds_*()
 constexpr int kBoundsCopiesSingle = 32;                 // spread atomics when nsims == 1
 
@@ -578,7 +581,7 @@ struct Workspace {
     uint32_t *perm2;       // [n]
     ug_grid_info *geo;     // [nsims]
     uint32_t *bounds;      // [copies * nsims * 8]
-    uint32_t *tile_sum;    // [ntiles]        rows per scan tile, zero between steps
+    uint32_t *tile_sum;    // [ntiles * kTileSumStride]  rows per scan tile, zero between steps
     Ctrl *ctrl;
     uint32_t ntiles;
     size_t bytes;
