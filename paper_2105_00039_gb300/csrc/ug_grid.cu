@@ -43,8 +43,9 @@ k_bounds(const float4 *__restrict__ st, SimArgs sa, uint32_t *bounds, ug_grid_in
 // Each warp covers 2 x 32 consecutive rows (kKeyItems chunks), so that two
 // independent chains of loads and atomics are in flight per thread.
 constexpr int kKeyItems = 2;
+constexpr int kKeyWarps = 8;   // 256 threads
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kKeyWarps * 32)
 k_key(const float4 *__restrict__ st, SimArgs sa, const ug_grid_info *__restrict__ geo,
       uint32_t *counts, uint32_t *tile_sum, uint32_t *__restrict__ key,
       uint32_t *__restrict__ rank, ug_grid_info *geo_save, int32_t *status) {
@@ -54,6 +55,7 @@ k_key(const float4 *__restrict__ st, SimArgs sa, const ug_grid_info *__restrict_
     if (geo_save)
         for (uint32_t s = gtid; s < sa.nsims; s += stride) geo_save[s] = geo[s];
     if (cta_failed(status)) return;
+    __shared__ uint32_t s_tile[kKeyWarps * kKeyItems], s_rows[kKeyWarps * kKeyItems];
 
     const int lane = threadIdx.x & 31;
     const uint32_t first = blockIdx.x * blockDim.x * kKeyItems;
@@ -89,23 +91,46 @@ k_key(const float4 *__restrict__ st, SimArgs sa, const ug_grid_info *__restrict_
         const int nexthead = after ? __ffs(after) - 1 : 32;
         uint32_t base = 0;
         if (head && valid) base = atomicAdd(&counts[k], (uint32_t)(nexthead - lane));
-        // rows per scan tile: one atomic per warp when its rows share a tile
+        // rows per scan tile: a warp whose rows share one tile reports a single
+        // (tile, rows) pair for the CTA to merge below; otherwise its lanes add
+        // their own rows (a warp that straddles a tile boundary)
         const unsigned vmask = __ballot_sync(kFull, valid);
+        uint32_t wtile = 0, wrows = 0;
         if (vmask) {
             const uint32_t tl = k >> kScanTileShift;
             const uint32_t tl0 = __shfl_sync(kFull, tl, __ffs(vmask) - 1);
             if (__all_sync(kFull, !valid || tl == tl0)) {
-                if (lane == __ffs(vmask) - 1)
-                    atomicAdd(&tile_sum[tl0 * kTileSumStride], (uint32_t)__popc(vmask));
+                wtile = tl0;
+                wrows = (uint32_t)__popc(vmask);
             } else if (valid) {
                 atomicAdd(&tile_sum[tl * kTileSumStride], 1u);
             }
+        }
+        if (lane == 0) {
+            s_tile[(threadIdx.x >> 5) * kKeyItems + it] = wtile;
+            s_rows[(threadIdx.x >> 5) * kKeyItems + it] = wrows;
         }
         base = __shfl_sync(kFull, base, myhead);
         if (valid) {
             rank[i] = base + (uint32_t)(lane - myhead);
             key[i] = k;
         }
+    }
+    // one atomic per run of equal tiles among the CTA's warp reports (the rows
+    // arrive nearly sorted, so usually one per CTA)
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t cur = 0, acc = 0;
+        for (int e = 0; e < kKeyWarps * kKeyItems; ++e) {
+            if (s_rows[e] == 0u) continue;
+            if (acc != 0u && s_tile[e] != cur) {
+                atomicAdd(&tile_sum[cur * kTileSumStride], acc);
+                acc = 0u;
+            }
+            cur = s_tile[e];
+            acc += s_rows[e];
+        }
+        if (acc != 0u) atomicAdd(&tile_sum[cur * kTileSumStride], acc);
     }
 }
 
@@ -266,7 +291,7 @@ void launch_bounds(const float4 *st, const SimArgs &sa, const Workspace &w, ug_g
 
 void launch_key(const float4 *st, const SimArgs &sa, const Workspace &w, const ug_grid_info *geo,
                 ug_grid_info *geo_save, int32_t *status, cudaStream_t s) {
-    launch_chained(k_key, blocks_for(sa.n, 256 * kKeyItems), 256, s, st, sa, geo, w.counts, w.tile_sum,
+    launch_chained(k_key, blocks_for(sa.n, kKeyWarps * 32 * kKeyItems), kKeyWarps * 32, s, st, sa, geo, w.counts, w.tile_sum,
                    w.key, w.rank, geo_save, status);
 }
 
