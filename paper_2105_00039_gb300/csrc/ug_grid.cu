@@ -69,35 +69,41 @@ k_key(const float4 *__restrict__ st, SimArgs sa, const ug_grid_info *__restrict_
         idx[it] = wbase + 32u * it + lane;
         p[it] = idx[it] < sa.n ? __ldg(st + idx[it]) : make_float4(0.f, 0.f, 0.f, 1.f);
     }
+    uint32_t k[kKeyItems], base[kKeyItems];
+    int myhead[kKeyItems], nrun[kKeyItems];
 #pragma unroll
     for (int it = 0; it < kKeyItems; ++it) {
-        const uint32_t i = idx[it];
-        const bool valid = i < sa.n;
-        uint32_t k = 0xffffffffu;
-        if (valid) {
-            const uint32_t sim = uniform ? csim : find_sim(sa, i);
+        k[it] = 0xffffffffu;
+        if (idx[it] < sa.n) {
+            const uint32_t sim = uniform ? csim : find_sim(sa, idx[it]);
             const ug_grid_info g = geo[sim];
             int bx, by, bz;
-            k = box_key(p[it], g, bx, by, bz);
+            k[it] = box_key(p[it], g, bx, by, bz);
         }
         // rows arrive nearly sorted by box (the previous step's order), so equal
         // keys mostly sit on consecutive lanes: each run of equal keys takes one
         // atomic, and its lanes get consecutive provisional ranks
-        const uint32_t prevk = __shfl_up_sync(kFull, k, 1);
-        const bool head = lane == 0 || prevk != k;
+        const uint32_t prevk = __shfl_up_sync(kFull, k[it], 1);
+        const bool head = lane == 0 || prevk != k[it];
         const unsigned heads = __ballot_sync(kFull, head);
-        const int myhead = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+        myhead[it] = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
         const unsigned after = lane == 31 ? 0u : heads & (0xffffffffu << (lane + 1));
-        const int nexthead = after ? __ffs(after) - 1 : 32;
-        uint32_t base = 0;
-        if (head && valid) base = atomicAdd(&counts[k], (uint32_t)(nexthead - lane));
-        // rows per scan tile: a warp whose rows share one tile reports a single
-        // (tile, rows) pair for the CTA to merge below; otherwise its lanes add
-        // their own rows (a warp that straddles a tile boundary)
+        nrun[it] = head && idx[it] < sa.n ? (after ? __ffs(after) - 1 : 32) - lane : 0;
+    }
+    // all the histogram atomics first, so that their round trips overlap
+#pragma unroll
+    for (int it = 0; it < kKeyItems; ++it)
+        base[it] = nrun[it] > 0 ? atomicAdd(&counts[k[it]], (uint32_t)nrun[it]) : 0u;
+    // rows per scan tile: a warp whose rows share one tile reports a single
+    // (tile, rows) pair for the CTA to merge below; otherwise its lanes add
+    // their own rows (a warp that straddles a tile boundary)
+#pragma unroll
+    for (int it = 0; it < kKeyItems; ++it) {
+        const bool valid = idx[it] < sa.n;
         const unsigned vmask = __ballot_sync(kFull, valid);
         uint32_t wtile = 0, wrows = 0;
         if (vmask) {
-            const uint32_t tl = k >> kScanTileShift;
+            const uint32_t tl = k[it] >> kScanTileShift;
             const uint32_t tl0 = __shfl_sync(kFull, tl, __ffs(vmask) - 1);
             if (__all_sync(kFull, !valid || tl == tl0)) {
                 wtile = tl0;
@@ -110,10 +116,13 @@ k_key(const float4 *__restrict__ st, SimArgs sa, const ug_grid_info *__restrict_
             s_tile[(threadIdx.x >> 5) * kKeyItems + it] = wtile;
             s_rows[(threadIdx.x >> 5) * kKeyItems + it] = wrows;
         }
-        base = __shfl_sync(kFull, base, myhead);
-        if (valid) {
-            rank[i] = base + (uint32_t)(lane - myhead);
-            key[i] = k;
+    }
+#pragma unroll
+    for (int it = 0; it < kKeyItems; ++it) {
+        const uint32_t b = __shfl_sync(kFull, base[it], myhead[it]);
+        if (idx[it] < sa.n) {
+            rank[idx[it]] = b + (uint32_t)(lane - myhead[it]);
+            key[idx[it]] = k[it];
         }
     }
     // one atomic per run of equal tiles among the CTA's warp reports (the rows
