@@ -39,7 +39,7 @@ size_t layout_workspace(void *base, uint32_t n, uint32_t nsims, uint32_t max_box
     };
     w->ctrl = reinterpret_cast<Ctrl *>(take(sizeof(Ctrl)));
     w->ntiles = std::max<uint32_t>(1u, (uint32_t)(((size_t)max_boxes + kScanTile - 1) / kScanTile));
-    w->tile_sum = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * kTileSumStride * (size_t)w->ntiles));
+    w->tile_sum = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * kTileSumStride * kTileCopies * (size_t)w->ntiles));
     w->counts = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (size_t)max_boxes));
     w->bounds = reinterpret_cast<uint32_t *>(
         take(sizeof(uint32_t) * kBoundsWords * (size_t)bounds_copies(nsims) * nsims));

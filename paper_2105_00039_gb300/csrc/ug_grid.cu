@@ -44,6 +44,7 @@ k_bounds(const float4 *__restrict__ st, SimArgs sa, uint32_t *bounds, ug_grid_in
 // independent chains of loads and atomics are in flight per thread.
 constexpr int kKeyItems = 2;
 constexpr int kKeyWarps = 8;   // 256 threads
+constexpr int kTilePairs = 3;  // tile sums added by lane 0 per warp and row chunk
 
 __global__ void __launch_bounds__(kKeyWarps * 32)
 k_key(const float4 *__restrict__ st, SimArgs sa, const ug_grid_info *__restrict__ geo,
@@ -55,7 +56,6 @@ k_key(const float4 *__restrict__ st, SimArgs sa, const ug_grid_info *__restrict_
     if (geo_save)
         for (uint32_t s = gtid; s < sa.nsims; s += stride) geo_save[s] = geo[s];
     if (cta_failed(status)) return;
-    __shared__ uint32_t s_tile[kKeyWarps * kKeyItems], s_rows[kKeyWarps * kKeyItems];
 
     const int lane = threadIdx.x & 31;
     const uint32_t first = blockIdx.x * blockDim.x * kKeyItems;
@@ -94,28 +94,29 @@ k_key(const float4 *__restrict__ st, SimArgs sa, const ug_grid_info *__restrict_
 #pragma unroll
     for (int it = 0; it < kKeyItems; ++it)
         base[it] = nrun[it] > 0 ? atomicAdd(&counts[k[it]], (uint32_t)nrun[it]) : 0u;
-    // rows per scan tile: a warp whose rows share one tile reports a single
-    // (tile, rows) pair for the CTA to merge below; otherwise its lanes add
-    // their own rows (a warp that straddles a tile boundary)
+    // rows per scan tile, added into this warp's copy of the tile sums: lane 0
+    // adds the rows of up to kTilePairs tiles (rows move between boxes every
+    // step, so a warp often holds rows of the tiles either side of its own);
+    // lanes of any further tile (rare) add their own rows
+    const uint32_t copy = (blockIdx.x * kKeyWarps + (threadIdx.x >> 5)) % kTileCopies;
+    auto tile_add = [&](uint32_t t, uint32_t rows) {
+        atomicAdd(&tile_sum[(t * kTileCopies + copy) * kTileSumStride], rows);
+    };
 #pragma unroll
     for (int it = 0; it < kKeyItems; ++it) {
         const bool valid = idx[it] < sa.n;
-        const unsigned vmask = __ballot_sync(kFull, valid);
-        uint32_t wtile = 0, wrows = 0;
-        if (vmask) {
-            const uint32_t tl = k[it] >> kScanTileShift;
-            const uint32_t tl0 = __shfl_sync(kFull, tl, __ffs(vmask) - 1);
-            if (__all_sync(kFull, !valid || tl == tl0)) {
-                wtile = tl0;
-                wrows = (uint32_t)__popc(vmask);
-            } else if (valid) {
-                atomicAdd(&tile_sum[tl * kTileSumStride], 1u);
+        const uint32_t tl = k[it] >> kScanTileShift;
+        unsigned rest = __ballot_sync(kFull, valid);
+#pragma unroll
+        for (int j = 0; j < kTilePairs; ++j) {
+            if (rest) {
+                const uint32_t tj = __shfl_sync(kFull, tl, __ffs(rest) - 1);
+                const unsigned mj = __ballot_sync(kFull, valid && tl == tj);
+                rest &= ~mj;
+                if (lane == 0) tile_add(tj, (uint32_t)__popc(mj));
             }
         }
-        if (lane == 0) {
-            s_tile[(threadIdx.x >> 5) * kKeyItems + it] = wtile;
-            s_rows[(threadIdx.x >> 5) * kKeyItems + it] = wrows;
-        }
+        if ((rest >> lane) & 1u) tile_add(tl, 1u);
     }
 #pragma unroll
     for (int it = 0; it < kKeyItems; ++it) {
@@ -125,28 +126,12 @@ k_key(const float4 *__restrict__ st, SimArgs sa, const ug_grid_info *__restrict_
             key[idx[it]] = k[it];
         }
     }
-    // one atomic per run of equal tiles among the CTA's warp reports (the rows
-    // arrive nearly sorted, so usually one per CTA)
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t cur = 0, acc = 0;
-        for (int e = 0; e < kKeyWarps * kKeyItems; ++e) {
-            if (s_rows[e] == 0u) continue;
-            if (acc != 0u && s_tile[e] != cur) {
-                atomicAdd(&tile_sum[cur * kTileSumStride], acc);
-                acc = 0u;
-            }
-            cur = s_tile[e];
-            acc += s_rows[e];
-        }
-        if (acc != 0u) atomicAdd(&tile_sum[cur * kTileSumStride], acc);
-    }
 }
 
 // ------------------------------------------------------------------ tile scan
 // CTA t scans boxes [t * kScanTile, (t + 1) * kScanTile).  Its exclusive
 // prefix, the rows in all earlier boxes, is the sum of the earlier tiles' row
-// counts that k_key accumulated, so no CTA waits on another.
+// counts that k_key accumulated (all copies), so no CTA waits on another.
 __global__ void __launch_bounds__(kScanThreads)
 k_scan(uint32_t *__restrict__ counts, uint32_t *__restrict__ start, const Ctrl *ctrl,
        const uint32_t *__restrict__ tile_sum, int32_t *status) {
@@ -161,7 +146,7 @@ k_scan(uint32_t *__restrict__ counts, uint32_t *__restrict__ start, const Ctrl *
     if (t >= ntiles) return;
     {
         uint32_t pre = 0;
-        for (uint32_t u = threadIdx.x; u < t; u += kScanThreads)
+        for (uint32_t u = threadIdx.x; u < t * kTileCopies; u += kScanThreads)
             pre += __ldg(tile_sum + (size_t)u * kTileSumStride);
         pre = __reduce_add_sync(kFull, pre);
         if (lane == 0) s_pre[warp] = pre;
@@ -234,7 +219,8 @@ k_place(const uint32_t *__restrict__ key, const uint32_t *__restrict__ rank,
         uint32_t *__restrict__ tile_sum, uint32_t ntiles, int32_t *status) {
     chain_begin();
     // the scan has consumed the tile sums: clear them for the next rebuild
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x)
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles * kTileCopies;
+         t += gridDim.x * blockDim.x)
         tile_sum[(size_t)t * kTileSumStride] = 0u;
     if (cta_failed(status)) return;
     const uint32_t i0 = blockIdx.x * blockDim.x * 2u + threadIdx.x, i1 = i0 + blockDim.x;

@@ -16,9 +16,12 @@ constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;   // boxes per scan tile (a power of 2)
 constexpr int kScanTileShift = 13;
 static_assert(kScanTile == 1 << kScanTileShift, "scan tile must be 2^kScanTileShift boxes");
-// Each tile's row count sits on its own 128-byte line (tile_sum[t * kTileSumStride]),
-// so that the histogram's per-warp atomics spread over L2 slices.
+// Row counts per scan tile, kept as kTileCopies partial sums per tile (copy c
+// of tile t at tile_sum[(t * kTileCopies + c) * kTileSumStride], each on its own
+// 128-byte line), so that the histogram's per-warp atomics spread over many
+// L2 lines instead of queueing on one per tile.
 constexpr uint32_t kTileSumStride = 32;
+constexpr uint32_t kTileCopies = 8;
 constexpr int kBoundsWords = 8;                         // per simulation, see bounds_*()
 constexpr int kBoundsCopiesSingle = 32;                 // spread atomics when nsims == 1
 
@@ -581,7 +584,7 @@ struct Workspace {
     uint32_t *perm2;       // [n]
     ug_grid_info *geo;     // [nsims]
     uint32_t *bounds;      // [copies * nsims * 8]
-    uint32_t *tile_sum;    // [ntiles * kTileSumStride]  rows per scan tile, zero between steps
+    uint32_t *tile_sum;    // [ntiles * kTileCopies * kTileSumStride]  zero between steps
     Ctrl *ctrl;
     uint32_t ntiles;
     size_t bytes;

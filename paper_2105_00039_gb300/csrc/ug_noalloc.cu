@@ -30,7 +30,7 @@ constexpr size_t up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 constexpr size_t kNoAllocTiles = (kNoAllocMaxBoxes + ug::kScanTile - 1) / ug::kScanTile;
 // ctrl | tile sums | counts | bounds (these four are zeroed per call) | key | rank | tmp
 constexpr size_t kOffTiles = up(sizeof(ug::Ctrl));
-constexpr size_t kOffCounts = kOffTiles + up(4ull * ug::kTileSumStride * kNoAllocTiles);
+constexpr size_t kOffCounts = kOffTiles + up(4ull * ug::kTileSumStride * ug::kTileCopies * kNoAllocTiles);
 constexpr size_t kOffBounds = kOffCounts + up(4ull * kNoAllocMaxBoxes);
 constexpr size_t kOffKey = kOffBounds + up(4ull * ug::kBoundsWords * ug::kBoundsCopiesSingle);
 constexpr size_t kOffRank = kOffKey + up(4ull * kNoAllocMaxAgents);
