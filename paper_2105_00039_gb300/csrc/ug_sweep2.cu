@@ -6,13 +6,14 @@
 // boxes [bx(2l) - 1, bx(2l+1) + 1]: every candidate row is loaded once and
 // tested against both agents, which halves the per-candidate index, load and
 // loop work of the one-agent-per-lane sweep.  A lane whose two agents lie too
-// far apart in box order to merge walks the two 9-run sets one after the other.  Runs are
-// walked in warp lockstep (trip count = the warp's longest run) with clamped
-// indices and masks, candidates that pass the packed float32 pre-filter go to
-// per-agent lists, and the exact float-float contact test and Eq. 1 run in
-// warp-converged batches.  k_sweep2 serves one simulation; k_sweep2m serves
-// many (a lane whose agents belong to different simulations walks them
-// separately, each with its own simulation's grid and constants).
+// far apart in box order to merge walks the two 9-run sets one after the
+// other.  Runs are walked in warp lockstep (trip count = the warp's longest
+// run; k_sweep2 concatenates the three runs of each neighbour plane) with
+// clamped indices and masks, candidates that pass the packed float32
+// pre-filter go to per-agent lists, and the exact float-float contact test and
+// Eq. 1 run in warp-converged batches.  k_sweep2 serves one simulation;
+// k_sweep2m serves many (a lane whose agents belong to different simulations
+// walks them separately, each with its own simulation's grid and constants).
 #include <cuda_runtime.h>
 
 #include "ug_internal.cuh"
@@ -101,30 +102,44 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
         c0 = 0;
         c1 = 0;
     };
-    const int nruns = __any_sync(kFull, split) ? 18 : 9;
+    // The 9 runs are walked as 3 sequences, one per neighbour plane (dz), each
+    // the plane's three runs (dy = -1, 0, +1) back to back: candidate t of a
+    // lane is row t + d0 while t < e1, t + d1 while t < e2, else t + d2.  A
+    // warp's trip count is then its longest sequence rather than the sum of
+    // its longest runs.  Groups 0..2 serve both agents (or agent 0 alone when
+    // split), 3..5 agent 1 when split.
+    const int ngroups = __any_sync(kFull, split) ? 6 : 3;
 #pragma unroll 1
-    for (int r = 0; r < nruns; ++r) {
-        // runs 0..8 serve both agents (or agent 0 alone when split), 9..17 agent 1 when split
-        const int rr = r < 9 ? r : r - 9;
-        const int off = (rr / 3 - 1) * plane + (rr % 3 - 1) * (int)dx;
+    for (int gi = 0; gi < ngroups; ++gi) {
+        const int dz = (gi < 3 ? gi : gi - 3) - 1;
         bool s0 = false, s1 = false;
-        uint32_t b = v0 ? i0 : 0u;     // a row that exists; masked off when len == 0
-        int len = 0;
-        if (v0 && (r < 9 || split)) {
+        uint32_t d0 = v0 ? i0 : 0u, d1 = d0, d2 = d0;
+        int e1 = 0, e2 = 0, len = 0;
+        if (v0 && (gi < 3 || split)) {
             uint32_t lo, hi;
             if (!split) { lo = k0; hi = k1; s0 = true; s1 = v1; }
-            else if (r < 9) { lo = k0; hi = k0; s0 = true; }
+            else if (gi < 3) { lo = k0; hi = k0; s0 = true; }
             else { lo = k1; hi = k1; s1 = true; }
-            b = __ldg(start + (uint32_t)((int)lo + off) - 1u);
-            len = (int)(__ldg(start + (uint32_t)((int)hi + off) + 2u) - b);
-            if (len == 0) b = i0;
+            const uint32_t lz = (uint32_t)((int)lo + dz * plane), hz = (uint32_t)((int)hi + dz * plane);
+            const uint32_t b0 = __ldg(start + lz - dx - 1u), x0 = __ldg(start + hz - dx + 2u);
+            const uint32_t b1 = __ldg(start + lz - 1u), x1 = __ldg(start + hz + 2u);
+            const uint32_t b2 = __ldg(start + lz + dx - 1u), x2 = __ldg(start + hz + dx + 2u);
+            e1 = (int)(x0 - b0);
+            e2 = e1 + (int)(x1 - b1);
+            len = e2 + (int)(x2 - b2);
+            if (len > 0) {
+                d0 = b0;
+                d1 = b1 - (uint32_t)e1;
+                d2 = b2 - (uint32_t)e2;
+            }
         }
         const int last = max(len - 1, 0);
         const int lmax = (int)__reduce_max_sync(kFull, (unsigned)len);
         for (int t = 0; t < lmax; t += kSweepUnroll) {
 #pragma unroll
             for (int u = 0; u < kSweepUnroll; ++u) {
-                const uint32_t jc = b + (uint32_t)min(t + u, last);
+                const int tt = min(t + u, last);
+                const uint32_t jc = (uint32_t)tt + (tt < e1 ? d0 : (tt < e2 ? d1 : d2));
                 const float4 q = __ldg(st + jc);
                 const bool in = t + u < len;
                 if (in & s0 & (jc != i0) & prefilter(q, f0)) {
