@@ -36,7 +36,8 @@ k_bounds(const float4 *__restrict__ st, SimArgs sa, uint32_t *bounds, ug_grid_in
     const uint32_t sim = cta_sim(sa, first, i, uniform);
     const float4 p = valid ? __ldg(st + i) : make_float4(0.f, 0.f, 0.f, 1.f);
     accumulate_bounds(sa, p, valid, sim, uniform, bounds, status);
-    if (elect_last_cta(&ctrl->done)) finalize_grid(sa, bounds, geo, ctrl, max_boxes, status);
+    __shared__ FinalizeScratch fs;
+    if (elect_last_cta(&ctrl->done)) finalize_grid(sa, bounds, geo, ctrl, max_boxes, status, fs);
 }
 
 // ------------------------------------------------------------------ key + histogram

@@ -423,11 +423,13 @@ __device__ __forceinline__ bool row_ok(const float4 &p) {
 }
 
 // Accumulate per-thread bounds codes (see bounds_codes; 0 = nothing); every
-// thread of the CTA calls it.
+// thread of the CTA calls it.  `red` is shared-memory scratch: warp w uses the
+// 8 words at red + w * red_stride (a kernel may point them into memory its
+// warps no longer need, each warp into its own part).
 __device__ __forceinline__ void accumulate_bounds_codes(const SimArgs &sa, uint32_t v[8],
                                                         bool valid, uint32_t sim, bool uniform,
-                                                        uint32_t *bounds) {
-    __shared__ uint32_t s_red[32][kBoundsWords];
+                                                        uint32_t *bounds, uint32_t *red,
+                                                        uint32_t red_stride) {
     const uint32_t copy = sa.bounds_copies > 1 ? blockIdx.x % sa.bounds_copies : 0u;
     if (uniform) {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -435,13 +437,13 @@ __device__ __forceinline__ void accumulate_bounds_codes(const SimArgs &sa, uint3
         for (int k = 0; k < 8; ++k) v[k] = __reduce_max_sync(kFull, v[k]);
         if (lane == 0) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) s_red[warp][k] = v[k];
+            for (int k = 0; k < 8; ++k) red[warp * red_stride + k] = v[k];
         }
         __syncthreads();
         if (threadIdx.x < 8) {
             uint32_t m = 0;
             const int nw = (blockDim.x + 31) >> 5;
-            for (int w = 0; w < nw; ++w) m = max(m, s_red[w][threadIdx.x]);
+            for (int w = 0; w < nw; ++w) m = max(m, red[w * red_stride + threadIdx.x]);
             if (m) atomicMax(&bounds[((size_t)copy * sa.nsims + sim) * kBoundsWords + threadIdx.x], m);
         }
     } else if (valid) {
@@ -455,28 +457,40 @@ __device__ __forceinline__ void accumulate_bounds_codes(const SimArgs &sa, uint3
 __device__ __forceinline__ void accumulate_bounds(const SimArgs &sa, const float4 &p, bool valid,
                                                   uint32_t sim, bool uniform, uint32_t *bounds,
                                                   int32_t *status) {
+    __shared__ uint32_t s_red[32 * kBoundsWords];
     if (valid && !row_ok(p)) set_status(status, UG_EBADSTATE);
     uint32_t v[8];
     bounds_codes(p, valid, v);
-    accumulate_bounds_codes(sa, v, valid, sim, uniform, bounds);
+    accumulate_bounds_codes(sa, v, valid, sim, uniform, bounds, s_red, kBoundsWords);
 }
+
+// Shared-memory scratch of finalize_grid (blockDim.x <= 256 for every caller).
+constexpr uint32_t kFinalizeChunk = 64;   // simulations finalised per pass (at most)
+struct FinalizeScratch {
+    unsigned long long scan[256];
+    uint32_t w[kFinalizeChunk][kBoundsWords];
+    unsigned long long carry;
+    int bad;
+};
 
 // Run by the last CTA to finish: turn the bounds into each simulation's grid,
 // assign box ranges, check capacity, and reset the accumulators for next time.
+// `fs` may point into shared memory the CTA no longer needs.
 __device__ __forceinline__ void finalize_grid(const SimArgs &sa, uint32_t *bounds,
                                               ug_grid_info *geo, Ctrl *ctrl, uint32_t max_boxes,
-                                              int32_t *status) {
-    __shared__ unsigned long long s_scan[256];   // blockDim.x <= 256 for every caller
-    constexpr uint32_t kChunk = 64;              // simulations finalised per pass
-    __shared__ uint32_t s_w[kChunk][kBoundsWords];
-    __shared__ unsigned long long s_carry;
-    __shared__ int s_bad;
+                                              int32_t *status, FinalizeScratch &fs) {
+    unsigned long long *s_scan = fs.scan;
+    constexpr uint32_t kChunk = kFinalizeChunk;
+    uint32_t (*s_w)[kBoundsWords] = fs.w;
+    unsigned long long &s_carry = fs.carry;
+    int &s_bad = fs.bad;
     const int tid = threadIdx.x, nt = blockDim.x;
     const uint32_t copies = sa.bounds_copies;
     if (tid == 0) { s_carry = 0; s_bad = 0; }
     __syncthreads();
-    for (uint32_t c0 = 0; c0 < sa.nsims; c0 += kChunk) {
-        const uint32_t nchunk = min(kChunk, sa.nsims - c0);
+    const uint32_t chunk = min(kChunk, (uint32_t)nt);   // one thread per simulation
+    for (uint32_t c0 = 0; c0 < sa.nsims; c0 += chunk) {
+        const uint32_t nchunk = min(chunk, sa.nsims - c0);
         // max over the copies of every word of this chunk, all threads at once,
         // resetting the accumulators for the next use
         for (uint32_t q = tid; q < nchunk * kBoundsWords; q += nt) s_w[q / kBoundsWords][q % kBoundsWords] = 0u;

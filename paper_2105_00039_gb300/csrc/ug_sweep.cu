@@ -249,8 +249,9 @@ k_sweep(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
         if (out.force) out.force[i] = make_float4(Fx, Fy, Fz, (moving ? 1.f : 0.f) + (capped ? 2.f : 0.f));
     }
     accumulate_bounds(sa, nw, valid, sim, uniform, out.bounds, status);
+    __shared__ FinalizeScratch fs;
     if (elect_last_cta(&out.ctrl->done))
-        finalize_grid(sa, out.bounds, out.geo_next, out.ctrl, out.max_boxes, status);
+        finalize_grid(sa, out.bounds, out.geo_next, out.ctrl, out.max_boxes, status, fs);
 }
 
 template <int MODE>

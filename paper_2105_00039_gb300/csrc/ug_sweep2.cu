@@ -20,9 +20,14 @@
 
 namespace ug {
 
-struct WarpLists2 {
-    uint32_t lst[2][kListCap][32];
+constexpr int kListCap2 = 16;   // candidates per agent between flushes
+
+struct __align__(16) WarpLists2 {
+    uint32_t lst[2][kListCap2][32];
 };
+static_assert(2 * sizeof(WarpLists2) >= sizeof(FinalizeScratch),
+              "the epilogue reuses the lists of a CTA of 2 or more warps");
+constexpr uint32_t kWarpListWords = sizeof(WarpLists2) / 4;
 
 struct Accum {
     float sx, sy, sz, cx, cy, cz;
@@ -151,7 +156,7 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
                     ++c1;
                 }
             }
-            if (__any_sync(kFull, max(c0, c1) > kListCap - kSweepUnroll)) flush();
+            if (__any_sync(kFull, max(c0, c1) > kListCap2 - kSweepUnroll)) flush();
         }
     }
     flush();
@@ -186,9 +191,14 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     bounds_codes(n1, v1, c2);
 #pragma unroll
     for (int k = 0; k < 8; ++k) codes[k] = max(codes[k], c2[k]);
-    accumulate_bounds_codes(sa, codes, v0, 0u, true, out.bounds);
+    // the epilogue's scratch lives in the warps' list memory, no longer needed:
+    // each warp's 8 bounds words in its own lists, the last CTA's grid
+    // finalisation across all of them
+    accumulate_bounds_codes(sa, codes, v0, 0u, true, out.bounds, &wl[0].lst[0][0][0],
+                                kWarpListWords);
     if (elect_last_cta(&out.ctrl->done))
-        finalize_grid(sa, out.bounds, out.geo_next, out.ctrl, out.max_boxes, status);
+        finalize_grid(sa, out.bounds, out.geo_next, out.ctrl, out.max_boxes, status,
+                      *reinterpret_cast<FinalizeScratch *>(wl));
 }
 
 template <int MODE, int T, bool MULTI>
@@ -284,7 +294,7 @@ k_sweep2m(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
                     ++c1;
                 }
             }
-            if (__any_sync(kFull, max(c0, c1) > kListCap - kSweepUnroll)) flush();
+            if (__any_sync(kFull, max(c0, c1) > kListCap2 - kSweepUnroll)) flush();
         }
     }
     flush();
@@ -320,13 +330,15 @@ k_sweep2m(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     if (uniform) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) codes[k] = max(codes[k], c2[k]);
-        accumulate_bounds_codes(sa, codes, v0, s0, true, out.bounds);
+        accumulate_bounds_codes(sa, codes, v0, s0, true, out.bounds, &wl[0].lst[0][0][0],
+                                kWarpListWords);
     } else {
-        accumulate_bounds_codes(sa, codes, v0, s0, false, out.bounds);
-        accumulate_bounds_codes(sa, c2, v1, s1, false, out.bounds);
+        accumulate_bounds_codes(sa, codes, v0, s0, false, out.bounds, nullptr, 0u);
+        accumulate_bounds_codes(sa, c2, v1, s1, false, out.bounds, nullptr, 0u);
     }
     if (elect_last_cta(&out.ctrl->done))
-        finalize_grid(sa, out.bounds, out.geo_next, out.ctrl, out.max_boxes, status);
+        finalize_grid(sa, out.bounds, out.geo_next, out.ctrl, out.max_boxes, status,
+                      *reinterpret_cast<FinalizeScratch *>(wl));
 }
 
 void launch_sweep2(int mode, const float4 *sorted, const uint32_t *start, const ug_grid_info *geo,
