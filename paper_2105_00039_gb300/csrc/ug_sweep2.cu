@@ -48,6 +48,22 @@ __device__ __forceinline__ void add_contact(const float4 &me, const float4 &q, f
     ++a.np;
 }
 
+// Exact contact test and Eq. 1 for the candidates listed since the last flush,
+// warp-converged (every lane calls it; trip count = the warp's longest list).
+// Out of line: the float-float contact test is long and runs a few times per
+// warp, so one copy of it serves every walk loop instead of one per loop.
+__device__ __noinline__ void flush_lists2(const float4 *__restrict__ st, const WarpLists2 *w,
+                                          int c0, int c1, float4 me0, float4 me1, float m2,
+                                          bool exact_diffs, ug_params P, Accum *a0, Accum *a1) {
+    const int lane = threadIdx.x & 31;
+    const int m0 = (int)__reduce_max_sync(kFull, (unsigned)c0);
+    for (int k = 0; k < m0; ++k)
+        if (k < c0) add_contact(me0, __ldg(st + w->lst[0][k][lane]), m2, exact_diffs, P, *a0);
+    const int m1 = (int)__reduce_max_sync(kFull, (unsigned)c1);
+    for (int k = 0; k < m1; ++k)
+        if (k < c1) add_contact(me1, __ldg(st + w->lst[1][k][lane]), m2, exact_diffs, P, *a1);
+}
+
 // The two agents' windows merge into one run per neighbour row, boxes
 // [k0 - 1, k1 + 1] shifted by the row's offset, when no two of the 9 merged
 // runs can overlap: the 9 offsets are at least one x-row (dims_x boxes) apart,
@@ -95,56 +111,22 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     const bool exact_diffs =
         __all_sync(kFull, (!v0 || far_from_origin(me0, g.edge)) && (!v1 || far_from_origin(me1, g.edge)));
     const FilterRow f0 = make_filter_row(me0, m2), f1 = make_filter_row(me1, m2);
-    Accum a0{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u}, a1{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u};
+    // the force sums are touched only by the flushes: kept in (local) memory
+    Accum acc[2] = {{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u}, {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u}};
     int c0 = 0, c1 = 0;
     auto flush = [&]() {
-        const int m0 = (int)__reduce_max_sync(kFull, (unsigned)c0);
-        for (int k = 0; k < m0; ++k)
-            if (k < c0) add_contact(me0, __ldg(st + w.lst[0][k][lane]), m2, exact_diffs, P, a0);
-        const int mm1 = (int)__reduce_max_sync(kFull, (unsigned)c1);
-        for (int k = 0; k < mm1; ++k)
-            if (k < c1) add_contact(me1, __ldg(st + w.lst[1][k][lane]), m2, exact_diffs, P, a1);
+        flush_lists2(st, &w, c0, c1, me0, me1, m2, exact_diffs, P, &acc[0], &acc[1]);
         c0 = 0;
         c1 = 0;
     };
-    // The 9 runs are walked as 3 sequences, one per neighbour plane (dz), each
-    // the plane's three runs (dy = -1, 0, +1) back to back: candidate t of a
-    // lane is row t + d0 while t < e1, t + d1 while t < e2, else t + d2.  A
-    // warp's trip count is then its longest sequence rather than the sum of
-    // its longest runs.  Groups 0..2 serve both agents (or agent 0 alone when
-    // split), 3..5 agent 1 when split.
-    const int ngroups = __any_sync(kFull, split) ? 6 : 3;
-#pragma unroll 1
-    for (int gi = 0; gi < ngroups; ++gi) {
-        const int dz = (gi < 3 ? gi : gi - 3) - 1;
-        bool s0 = false, s1 = false;
-        uint32_t d0 = v0 ? i0 : 0u, d1 = d0, d2 = d0;
-        int e1 = 0, e2 = 0, len = 0;
-        if (v0 && (gi < 3 || split)) {
-            uint32_t lo, hi;
-            if (!split) { lo = k0; hi = k1; s0 = true; s1 = v1; }
-            else if (gi < 3) { lo = k0; hi = k0; s0 = true; }
-            else { lo = k1; hi = k1; s1 = true; }
-            const uint32_t lz = (uint32_t)((int)lo + dz * plane), hz = (uint32_t)((int)hi + dz * plane);
-            const uint32_t b0 = __ldg(start + lz - dx - 1u), x0 = __ldg(start + hz - dx + 2u);
-            const uint32_t b1 = __ldg(start + lz - 1u), x1 = __ldg(start + hz + 2u);
-            const uint32_t b2 = __ldg(start + lz + dx - 1u), x2 = __ldg(start + hz + dx + 2u);
-            e1 = (int)(x0 - b0);
-            e2 = e1 + (int)(x1 - b1);
-            len = e2 + (int)(x2 - b2);
-            if (len > 0) {
-                d0 = b0;
-                d1 = b1 - (uint32_t)e1;
-                d2 = b2 - (uint32_t)e2;
-            }
-        }
+    // One lockstep walk over candidates [0, len) of this lane, candidate t being
+    // row index_of(t) (t clamped into the lane's range, masked when t >= len).
+    auto walk = [&](int len, int lmax, bool s0, bool s1, auto index_of) {
         const int last = max(len - 1, 0);
-        const int lmax = (int)__reduce_max_sync(kFull, (unsigned)len);
         for (int t = 0; t < lmax; t += kSweepUnroll) {
 #pragma unroll
             for (int u = 0; u < kSweepUnroll; ++u) {
-                const int tt = min(t + u, last);
-                const uint32_t jc = (uint32_t)tt + (tt < e1 ? d0 : (tt < e2 ? d1 : d2));
+                const uint32_t jc = index_of(min(t + u, last));
                 const float4 q = __ldg(st + jc);
                 const bool in = t + u < len;
                 if (in & s0 & (jc != i0) & prefilter(q, f0)) {
@@ -158,9 +140,47 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
             }
             if (__any_sync(kFull, max(c0, c1) > kListCap2 - kSweepUnroll)) flush();
         }
+    };
+    // The 9 runs come as 3 neighbour planes (dz) of 3 runs (dy = -1, 0, +1),
+    // and a warp walks each plane's three runs as one sequence: candidate t of
+    // a lane is row t + d0 while t < e1, t + d1 while t < e2, else t + d2.  The
+    // trip count is then the warp's longest concatenation rather than the sum
+    // of its longest runs, which pays where runs are short and uneven (sparse
+    // grids); every agent meets its candidates in the same order as run by
+    // run.  Planes 0..2 serve both agents (or agent 0 alone when split), 3..5
+    // agent 1 when split.
+    const int ngroups = __any_sync(kFull, split) ? 6 : 3;
+#pragma unroll 1
+    for (int gi = 0; gi < ngroups; ++gi) {
+        const int dz = (gi < 3 ? gi : gi - 3) - 1;
+        bool s0 = false, s1 = false;
+        uint32_t d0 = v0 ? i0 : 0u, d1 = d0, d2 = d0;   // a row that exists when len == 0
+        int e1 = 0, e2 = 0, len = 0;
+        if (v0 && (gi < 3 || split)) {
+            uint32_t lo, hi;
+            if (!split) { lo = k0; hi = k1; s0 = true; s1 = v1; }
+            else if (gi < 3) { lo = k0; hi = k0; s0 = true; }
+            else { lo = k1; hi = k1; s1 = true; }
+            const uint32_t lz = (uint32_t)((int)lo + dz * plane), hz = (uint32_t)((int)hi + dz * plane);
+            const uint32_t a0 = __ldg(start + lz - dx - 1u), x0 = __ldg(start + hz - dx + 2u);
+            const uint32_t a1 = __ldg(start + lz - 1u), x1 = __ldg(start + hz + 2u);
+            const uint32_t a2 = __ldg(start + lz + dx - 1u), x2 = __ldg(start + hz + dx + 2u);
+            e1 = (int)(x0 - a0);
+            e2 = e1 + (int)(x1 - a1);
+            len = e2 + (int)(x2 - a2);
+            if (len > 0) {
+                d0 = a0;
+                d1 = a1 - (uint32_t)e1;
+                d2 = a2 - (uint32_t)e2;
+            }
+        }
+        walk(len, (int)__reduce_max_sync(kFull, (unsigned)len), s0, s1, [&](int tt) {
+            return (uint32_t)tt + (tt < e1 ? d0 : (tt < e2 ? d1 : d2));
+        });
     }
     flush();
 
+    const Accum &a0 = acc[0], &a1 = acc[1];
     const float3 F0 = make_float3(a0.sx + a0.cx, a0.sy + a0.cy, a0.sz + a0.cz);
     const float3 F1 = make_float3(a1.sx + a1.cx, a1.sy + a1.cy, a1.sz + a1.cz);
     if (MODE == kSweepForce) {
