@@ -220,11 +220,12 @@ int ug_step_batched(float *state, uint32_t *perm, const uint32_t *sim_offset, ui
                     uint32_t max_boxes, const ug_tuning *tuning, void *ws, size_t ws_bytes,
                     int32_t *status, void *stream);
 
-/* Time the sweep with each candidate configuration (one agent per lane with 64
- * or 128 threads per CTA, two agents per lane) on the given batched problem and
- * write the fastest to *best (HOST pointer).  Needs ws_bytes >=
- * ug_workspace_bytes(n_total, nsims, max_boxes) + 16 * n_total + 512.
- * Synchronises the stream. */
+/* Time each candidate configuration (one agent per lane with 64 or 128 threads
+ * per CTA, two agents per lane) on the given batched problem -- three fused
+ * steps (grid build, sweep, move) of a scratch copy of the rows, after one
+ * untimed step -- and write the fastest to *best (HOST pointer).  `state` is
+ * only read.  Needs ws_bytes >= ug_workspace_bytes(n_total, nsims, max_boxes)
+ * + 20 * n_total + 768.  Synchronises the stream. */
 int ug_tune_batched(const float *state, const uint32_t *sim_offset, uint32_t nsims,
                     uint32_t n_total, const ug_params *params, uint32_t max_boxes,
                     ug_tuning *best, void *ws, size_t ws_bytes, void *stream);

@@ -311,11 +311,15 @@ int ug_tune_batched(const float *state, const uint32_t *sim_offset, uint32_t nsi
         return UG_EINVAL;
     Workspace w;
     const size_t base = layout_workspace(ws, n_total, nsims, max_boxes, &w);
-    const size_t need = base + align256(sizeof(float4) * (size_t)n_total) + 256;
+    const size_t rows_bytes = align256(sizeof(float4) * (size_t)n_total);
+    const size_t ids_bytes = align256(sizeof(uint32_t) * (size_t)n_total);
+    const size_t need = base + rows_bytes + ids_bytes + 256;
     if (need > ws_bytes) return UG_EWORKSPACE;
-    float4 *force = reinterpret_cast<float4 *>(static_cast<char *>(ws) + base);
-    int32_t *status = reinterpret_cast<int32_t *>(static_cast<char *>(ws) + base +
-                                                  align256(sizeof(float4) * (size_t)n_total));
+    // scratch copies of the rows and ids, advanced by a few fused steps per candidate
+    char *extra = static_cast<char *>(ws) + base;
+    float4 *rows = reinterpret_cast<float4 *>(extra);
+    uint32_t *ids = reinterpret_cast<uint32_t *>(extra + rows_bytes);
+    int32_t *status = reinterpret_cast<int32_t *>(extra + rows_bytes + ids_bytes);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     SimArgs sa{};
     sa.offset = sim_offset;
@@ -323,34 +327,35 @@ int ug_tune_batched(const float *state, const uint32_t *sim_offset, uint32_t nsi
     sa.nsims = nsims;
     sa.n = n_total;
     sa.bounds_copies = bounds_copies(nsims);
-    if (cudaMemsetAsync(w.ctrl, 0, zero_bytes(w), s) != cudaSuccess) return UG_ECUDA;
     if (cudaMemsetAsync(status, 0, sizeof(int32_t), s) != cudaSuccess) return UG_ECUDA;
-    const float4 *in = reinterpret_cast<const float4 *>(state);
-    launch_bounds(in, sa, w, w.geo, max_boxes, status, s);
-    launch_key(in, sa, w, w.geo, nullptr, status, s);
-    launch_scan(w, w.start, max_boxes, status, s);
-    launch_place(w, w.start, n_total, status, s);
-    launch_canon(w, w.start, in, nullptr, w.sorted, w.perm2, nullptr, n_total, status, s);
+    auto reset = [&]() -> int {
+        if (cudaMemcpyAsync(rows, state, sizeof(float4) * (size_t)n_total, cudaMemcpyDeviceToDevice,
+                            s) != cudaSuccess)
+            return UG_ECUDA;
+        k_iota<<<(n_total + 255) / 256, 256, 0, s>>>(ids, n_total);
+        return last_launch();
+    };
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return UG_ECUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return UG_ECUDA; }
-    // candidates: (agents per lane, threads per CTA)
+    // candidates: (agents per lane, threads per CTA), each timed on kTuneSteps
+    // fused steps (grid build + sweep + move) from the given rows, after one
+    // untimed step
+    constexpr int kTuneSteps = 3;
     const int cands[3][2] = {{1, 64}, {1, 128}, {2, 128}};
     float best_ms = 1e30f;
     int rc = UG_OK;
     for (int c = 0; c < 3 && rc == UG_OK; ++c) {
-        SweepOut o{};
-        o.force = force;
-        auto sweep = [&]() {
-            if (cands[c][0] == 2)
-                launch_sweep2(kSweepForce, w.sorted, w.start, w.geo, sa, o, status, s, nullptr);
-            else
-                launch_sweep(kSweepForce, w.sorted, w.start, w.geo, sa, o, cands[c][1], status, s);
-        };
-        sweep();   // warm
+        rc = reset();
+        if (rc == UG_OK)
+            rc = run_steps(rows, ids, sa, 1, max_boxes, w, cands[c][1], cands[c][0], nullptr, status, s);
+        if (rc == UG_OK) rc = reset();
+        if (rc != UG_OK) break;
         cudaEventRecord(e0, s);
-        for (int rep = 0; rep < 3; ++rep) sweep();
+        rc = run_steps(rows, ids, sa, kTuneSteps, max_boxes, w, cands[c][1], cands[c][0], nullptr,
+                       status, s);
         cudaEventRecord(e1, s);
+        if (rc != UG_OK) break;
         if (cudaEventSynchronize(e1) != cudaSuccess) { rc = UG_ECUDA; break; }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);

@@ -440,7 +440,7 @@ def step_backward(ckpt_state, params: Params, nsteps: int, max_boxes: int, grad_
 def tune_batched(state, sim_offset, params_dev, nsims: int, max_boxes: int) -> ug_tuning:
     lib = load()
     n = state.shape[0]
-    ws = workspace(lib.ug_workspace_bytes(n, nsims, max_boxes) + 16 * n + 1024, state.device)
+    ws = workspace(lib.ug_workspace_bytes(n, nsims, max_boxes) + 20 * n + 1024, state.device)
     best = ug_tuning()
     rc = lib.ug_tune_batched(_ptr(state), _ptr(sim_offset), nsims, n, _ptr(params_dev), max_boxes,
                              ctypes.byref(best), _ptr(ws), ws.numel(), _stream())
