@@ -64,6 +64,20 @@ __device__ __noinline__ void flush_lists2(const float4 *__restrict__ st, const W
         if (k < c1) add_contact(me1, __ldg(st + w->lst[1][k][lane]), m2, exact_diffs, P, *a1);
 }
 
+// flush_lists2 for two agents that may belong to different simulations.
+__device__ __noinline__ void flush_lists2m(const float4 *__restrict__ st, const WarpLists2 *w,
+                                           int c0, int c1, float4 me0, float4 me1, float m20,
+                                           float m21, bool exact_diffs, ug_params P0,
+                                           ug_params P1, Accum *a0, Accum *a1) {
+    const int lane = threadIdx.x & 31;
+    const int m0 = (int)__reduce_max_sync(kFull, (unsigned)c0);
+    for (int k = 0; k < m0; ++k)
+        if (k < c0) add_contact(me0, __ldg(st + w->lst[0][k][lane]), m20, exact_diffs, P0, *a0);
+    const int m1 = (int)__reduce_max_sync(kFull, (unsigned)c1);
+    for (int k = 0; k < m1; ++k)
+        if (k < c1) add_contact(me1, __ldg(st + w->lst[1][k][lane]), m21, exact_diffs, P1, *a1);
+}
+
 // The two agents' windows merge into one run per neighbour row, boxes
 // [k0 - 1, k1 + 1] shifted by the row's offset, when no two of the 9 merged
 // runs can overlap: the 9 offsets are at least one x-row (dims_x boxes) apart,
@@ -266,15 +280,11 @@ k_sweep2m(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     const bool exact_diffs = __all_sync(kFull, (!v0 || far_from_origin(me0, g0.edge)) &&
                                                    (!v1 || far_from_origin(me1, g1.edge)));
     const FilterRow f0 = make_filter_row(me0, m20), f1 = make_filter_row(me1, m21);
-    Accum a0{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u}, a1{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u};
+    Accum acc[2] = {{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u}, {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u}};
+    Accum &a0 = acc[0], &a1 = acc[1];
     int c0 = 0, c1 = 0;
     auto flush = [&]() {
-        const int m0 = (int)__reduce_max_sync(kFull, (unsigned)c0);
-        for (int k = 0; k < m0; ++k)
-            if (k < c0) add_contact(me0, __ldg(st + w.lst[0][k][lane]), m20, exact_diffs, P0, a0);
-        const int mm1 = (int)__reduce_max_sync(kFull, (unsigned)c1);
-        for (int k = 0; k < mm1; ++k)
-            if (k < c1) add_contact(me1, __ldg(st + w.lst[1][k][lane]), m21, exact_diffs, P1, a1);
+        flush_lists2m(st, &w, c0, c1, me0, me1, m20, m21, exact_diffs, P0, P1, &acc[0], &acc[1]);
         c0 = 0;
         c1 = 0;
     };
