@@ -250,6 +250,33 @@ int ug_step_backward(const float *ckpt_state, uint32_t n, ug_params p, int32_t n
                      float *grad_params, void *ws, size_t ws_bytes, int32_t *status,
                      void *stream);
 
+/* ------------------------------------------------------------------ version ladder */
+
+/* The paper's GPU versions (Sec. IV-B to IV-E), for comparison with the main
+ * path only; it has no role in ug_step.  Forces of Eq. 1 on every agent of
+ * `state`, evaluated directly (delta = r_i + r_j + 2 contact_margin - d, plain
+ * sums) on the main path's grid geometry:
+ *   version 0  one thread per agent over per-box linked lists (each box keeps
+ *              its last agent, each agent the one added before it), rows in the
+ *              caller's order, float64 arithmetic
+ *   version 1  as 0 in float32
+ *   version 2  as 1 over box-sorted rows (the main path's counting sort)
+ *   version 3  one 32-thread CTA per box, the 27 boxes' agents appended to
+ *              shared memory through an atomic counter, float32, box-sorted
+ *              rows; a neighbourhood above 1024 agents records UG_ECAPACITY
+ *   state      [n] DEVICE rows (x, y, z, diameter), caller's order, 16-B aligned
+ *   force      [n][4] DEVICE float64 (fx, fy, fz, overlapping pairs), caller's
+ *              order, 16-B aligned
+ *   max_boxes  capacity of the grid (as for ug_grid_build)
+ *   ws         >= ug_ladder_workspace_bytes(n, max_boxes), 256-B aligned
+ * Versions 1-3 sum in an order set by atomics, so their float32 results may
+ * differ in the last bits from run to run.  Errors: UG_EINVAL (version outside
+ * 0..3, bad pointer or size), UG_EWORKSPACE, device errors as for ug_grid_build. */
+size_t ug_ladder_workspace_bytes(uint32_t n, uint32_t max_boxes);
+int ug_forces_ladder(int32_t version, const float *state, uint32_t n, ug_params p,
+                     uint32_t max_boxes, double *force, void *ws, size_t ws_bytes, int32_t *status,
+                     void *stream);
+
 /* ------------------------------------------------------------------ helpers */
 
 /* perm[i] = i. */

@@ -375,6 +375,37 @@ int ug_tune_batched(const float *state, const uint32_t *sim_offset, uint32_t nsi
     return rc;
 }
 
+size_t ug_ladder_workspace_bytes(uint32_t n, uint32_t max_boxes) {
+    Workspace w;
+    return layout_workspace(nullptr, n, 1, max_boxes, &w) + align256(sizeof(uint32_t) * (size_t)max_boxes) +
+           align256(sizeof(uint32_t) * (size_t)n);
+}
+
+int ug_forces_ladder(int32_t version, const float *state, uint32_t n, ug_params p,
+                     uint32_t max_boxes, double *force, void *ws, size_t ws_bytes, int32_t *status,
+                     void *stream) {
+    if (version < 0 || version > 3) return UG_EINVAL;
+    if (n == 0) return UG_OK;
+    if (!rows_ok(state) || !force || !aligned(force, 16) || !status || !ws || !aligned(ws, 256) ||
+        max_boxes < 27 || max_boxes > 0x7fffff00u || !(p.contact_margin >= 0.0f))
+        return UG_EINVAL;
+    if (ug_ladder_workspace_bytes(n, max_boxes) > ws_bytes) return UG_EWORKSPACE;
+    Workspace w;
+    const size_t base = layout_workspace(ws, n, 1, max_boxes, &w);
+    uint32_t *head = reinterpret_cast<uint32_t *>(static_cast<char *>(ws) + base);
+    uint32_t *next = reinterpret_cast<uint32_t *>(static_cast<char *>(ws) + base +
+                                                  align256(sizeof(uint32_t) * (size_t)max_boxes));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(w.ctrl, 0, zero_bytes(w), s) != cudaSuccess) return UG_ECUDA;
+    SimArgs sa{};
+    sa.nsims = 1;
+    sa.n = n;
+    sa.pval = p;
+    sa.bounds_copies = bounds_copies(1);
+    return run_ladder(version, reinterpret_cast<const float4 *>(state), n, sa, max_boxes, w, head,
+                      next, force, status, s);
+}
+
 int ug_iota(uint32_t *perm, uint32_t n, void *stream) {
     if (n == 0) return UG_OK;
     if (!perm) return UG_EINVAL;

@@ -605,6 +605,11 @@ struct Workspace {
 };
 
 size_t layout_workspace(void *base, uint32_t n, uint32_t nsims, uint32_t max_boxes, Workspace *w);
+// The paper's version ladder (ug_ladder.cu): forces of `state` (caller's order)
+// into force[4n] float64, with head[max_boxes] and next[n] as scratch.
+int run_ladder(int version, const float4 *state, uint32_t n, const SimArgs &sa, uint32_t max_boxes,
+               const Workspace &w, uint32_t *head, uint32_t *next, double *force, int32_t *status,
+               cudaStream_t s);
 int device_sm_count();
 
 // ------------------------------------------------------------------ launchers

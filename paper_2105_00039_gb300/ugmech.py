@@ -29,7 +29,7 @@ EXPORTED = ("ug_strerror", "ug_version", "ug_workspace_bytes", "ug_grid_build",
             "ug_step_traced",
             "ug_step_batched", "ug_tune_batched", "ug_backward_workspace_bytes",
             "ug_step_backward", "ug_iota", "ug_scatter_rows", "ug_gather_rows",
-            "ug_grid_build_noalloc")
+            "ug_grid_build_noalloc", "ug_ladder_workspace_bytes", "ug_forces_ladder")
 
 
 class UgError(RuntimeError):
@@ -103,6 +103,9 @@ _SIG = {
     "ug_step_backward": (ctypes.c_int, [_P, _U32, ug_params, ctypes.c_int32, _U32, _P, _P, _P,
                                         _P, ctypes.c_size_t, _P, _P]),
     "ug_iota": (ctypes.c_int, [_P, _U32, _P]),
+    "ug_ladder_workspace_bytes": (ctypes.c_size_t, [_U32, _U32]),
+    "ug_forces_ladder": (ctypes.c_int, [ctypes.c_int32, _P, _U32, ug_params, _U32, _P, _P,
+                                        ctypes.c_size_t, _P, _P]),
     "ug_scatter_rows": (ctypes.c_int, [_P, _P, _U32, _P, _P]),
     "ug_gather_rows": (ctypes.c_int, [_P, _P, _U32, _P, _P]),
 }
@@ -272,6 +275,26 @@ def list_pairs(state_sorted, box_start, info, contact_margin: float = 0.0,
     if check:
         check_status(status, "ug_list_pairs")
     return count, nbr
+
+
+def forces_ladder(state, version: int, params: Params = Params(), max_boxes: int | None = None,
+                  status=None, check: bool = True) -> torch.Tensor:
+    """The paper's GPU version `version` (0..3) of the force computation:
+    (Fx, Fy, Fz, contacts) per row in the caller's order, float64."""
+    lib = load()
+    _rows(state, "state")
+    n = state.shape[0]
+    if max_boxes is None:
+        max_boxes = estimate_max_boxes(state, params.contact_margin)
+    ws = workspace(lib.ug_ladder_workspace_bytes(n, max_boxes), state.device)
+    force = torch.empty((n, 4), dtype=torch.float64, device=state.device)
+    status = new_status(state.device) if status is None else status
+    rc = lib.ug_forces_ladder(int(version), _ptr(state), n, params.c(), max_boxes, _ptr(force),
+                              _ptr(ws), ws.numel(), _ptr(status), _stream())
+    _check(rc, "ug_forces_ladder")
+    if check:
+        check_status(status, "ug_forces_ladder")
+    return force
 
 
 def apply_displacement(state, force, params: Params = Params(), out=None, want_disp=True,

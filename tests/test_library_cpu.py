@@ -97,3 +97,21 @@ def test_argument_validation_without_device(lib):
                                     ctypes.c_uint32, P, P, ctypes.c_size_t, P, P]
     assert lib.ug_step_batched(fake, fake, fake, 0, 10, fake, 1, 100, None, fake, 1 << 30, fake,
                                None) == -1                                          # nsims = 0
+
+
+def test_ladder_validation_without_device(lib):
+    P = ctypes.c_void_p
+    lib.ug_ladder_workspace_bytes.restype = ctypes.c_size_t
+    lib.ug_forces_ladder.argtypes = [ctypes.c_int32, P, ctypes.c_uint32, _Params, ctypes.c_uint32,
+                                     P, P, ctypes.c_size_t, P, P]
+    p = _Params(2, 1, 0.1, 1, 0.02, 3, 0)
+    fake = ctypes.c_void_p(0x10000)
+    need = lib.ug_ladder_workspace_bytes(1000, 5000)
+    assert need >= lib.ug_workspace_bytes(1000, 1, 5000) + 4 * (1000 + 5000)
+    for bad_version in (-1, 4):
+        assert lib.ug_forces_ladder(bad_version, fake, 10, p, 100, fake, fake, 1 << 30, fake,
+                                    None) == -1
+    assert lib.ug_forces_ladder(0, fake, 0, p, 100, None, None, 0, None, None) == 0   # n = 0
+    assert lib.ug_forces_ladder(1, None, 10, p, 100, fake, fake, 1 << 30, fake, None) == -1
+    assert lib.ug_forces_ladder(2, fake, 10, p, 10, fake, fake, 1 << 30, fake, None) == -1
+    assert lib.ug_forces_ladder(3, fake, 1000, p, 5000, fake, fake, need - 1, fake, None) == -5
