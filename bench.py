@@ -361,6 +361,7 @@ def run_ours(args, world, rank, local, pg):
         line["batched"] = measure_batched(dev, flush)
         line["adjoint"] = measure_adjoint(dev, flush)
         line["density_sweep"] = measure_density(dev, flush)
+        line["version_ladder"] = measure_ladder(dev, flush)
 
     if rank == 0 and not args.no_cpu_baseline:
         rate, secs = cpu_oracle_rate(st, 3)
@@ -513,6 +514,60 @@ def measure_adjoint(dev, flush, side=64, nsteps=50, ckpt=10, reps=3):
     return {"workload": f"{side}^3 = {side ** 3} lattice cells, {nsteps} steps, checkpoint every {ckpt}",
             "forward_ms": f_ms, "backward_ms": b_ms, "plain_forward_ms": p_ms,
             "backward_over_forward": b_ms / f_ms, "backward_over_plain_forward": b_ms / p_ms}
+
+
+def measure_ladder(dev, flush, reps=3):
+    """The paper's GPU versions (Sec. IV-B to IV-E) beside the main path: one
+    force evaluation of the 2^20-cell lattice whose rows come in a seeded random
+    order (the order agents were created in, not a spatial one).  Each version's
+    whole call (grid + forces) and the main path's grid build + force sweep."""
+    import torch
+
+    from paper_2105_00039_gb300 import populations as P
+    from paper_2105_00039_gb300 import ugmech as U
+    st = P.lattice_1m(0)
+    n = len(st)
+    order = np.argsort(P.uniform01(7, 301, n), kind="stable")
+    x = torch.from_numpy(np.ascontiguousarray(st[order])).to(dev)
+    prm = U.Params()
+    lib = U.load()
+    mb = U.estimate_max_boxes(x, 0.0)
+    status = U.new_status(dev)
+    out = {"workload": "2^20-cell lattice (102^3 sites, spacing 9), rows in a seeded random order; "
+                       "one force evaluation including the grid"}
+    ws = U.workspace(lib.ug_ladder_workspace_bytes(n, mb), dev)
+    force = torch.empty((n, 4), dtype=torch.float64, device=dev)
+    names = ("version0_fp64_lists", "version1_fp32_lists", "version2_fp32_sorted_lists",
+             "version3_fp32_shared_atomics")
+    for v, name in enumerate(names):
+        def run(v=v):
+            U._check(lib.ug_forces_ladder(v, U._ptr(x), n, prm.c(), mb, U._ptr(force), U._ptr(ws),
+                                          ws.numel(), U._ptr(status), U._stream()), "ug_forces_ladder")
+        run()
+        U.check_status(status, "ug_forces_ladder")
+        ms = _timed(run, reps, flush)
+        U.check_status(status, "ug_forces_ladder")
+        out[name] = {"ms": ms, "agents_per_s": n / (ms / 1e3)}
+    del ws, force
+    srt = torch.empty_like(x)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    start = torch.empty(mb + 1, dtype=torch.int32, device=dev)
+    info = torch.empty(48, dtype=torch.uint8, device=dev)
+    ws = U.workspace(lib.ug_workspace_bytes(n, 1, mb), dev)
+    F = torch.empty_like(x)
+
+    def main():
+        U._check(lib.ug_grid_build(U._ptr(x), None, n, 0.0, U._ptr(srt), U._ptr(perm), U._ptr(start),
+                                   mb, U._ptr(info), U._ptr(ws), ws.numel(), U._ptr(status),
+                                   U._stream()), "ug_grid_build")
+        U._check(lib.ug_compute_forces(U._ptr(srt), U._ptr(start), U._ptr(info), n, prm.c(), U._ptr(F),
+                                       U._ptr(status), U._stream()), "ug_compute_forces")
+    main()
+    U.check_status(status, "main path")
+    ms = _timed(main, reps, flush)
+    U.check_status(status, "main path")
+    out["main_path_grid_build_plus_forces"] = {"ms": ms, "agents_per_s": n / (ms / 1e3)}
+    return out
 
 
 def measure_density(dev, flush, reps=2, nsteps=20):
