@@ -367,8 +367,25 @@ def run_ours(args, world, rank, local, pg):
         rate, secs = cpu_oracle_rate(st, 3)
         line["cpu_baseline"] = {"value": rate, "unit": "agent-steps/s", "cores": 1, "kind": "oracle",
                                 "sample": f"3 FP64 oracle steps of all 2^20 cells ({secs:.1f} s)"}
+        line["cpu_grid_baseline"] = cpu_grid_rate(st, 3)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def cpu_grid_rate(st, nsteps):
+    """The paper's CPU uniform-grid method (baseline/cpu_ug: float64, linked-list
+    grid rebuilt every step, OpenMP over agents) on all host cores: the CPU
+    comparison the paper's speedups are quoted against."""
+    try:
+        sys.path.insert(0, os.path.join(ROOT, "baseline", "cpu_ug"))
+        import cpu_ug
+        threads = cpu_ug.max_threads()
+        _, secs = cpu_ug.steps(st, nsteps, threads=threads)
+    except Exception as e:   # no g++ / OpenMP on this host
+        return {"unavailable": f"{type(e).__name__}: {e}"[:200]}
+    return {"value": len(st) * nsteps / secs, "unit": "agent-steps/s", "cores": threads,
+            "kind": "cpu uniform grid, float64, OpenMP",
+            "sample": f"{nsteps} steps of all {len(st)} cells ({secs:.2f} s)"}
 
 
 # ---------------------------------------------------------------------------- extra rows
