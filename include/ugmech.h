@@ -20,7 +20,7 @@
  *     256-byte aligned.  Its contents need not be initialised and are
  *     clobbered.
  *   - Agent state is float32, 4 floats per agent: (x, y, z, diameter), 16-byte
- *     aligned.  Forces and gradients use the same 4-float rows.
+ *     aligned.  At most 2^30 agents per call (UG_EINVAL above).  Forces and gradients use the same 4-float rows.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call is
  *     asynchronous: the return value reports argument and launch errors only.
  *     Errors found on the device (bad input values, grid too large, a list

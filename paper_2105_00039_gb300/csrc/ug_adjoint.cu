@@ -208,7 +208,7 @@ size_t ug_backward_workspace_bytes(uint32_t n, uint32_t max_boxes, int32_t nstep
 int ug_step_backward(const float *ckpt_state, uint32_t n, ug_params p, int32_t nsteps,
                      uint32_t max_boxes, const float *grad_out, float *grad_in, float *grad_params,
                      void *ws, size_t ws_bytes, int32_t *status, void *stream) {
-    if (nsteps < 0) return UG_EINVAL;
+    if (nsteps < 0 || n > kMaxAgents) return UG_EINVAL;
     if (!grad_params || !status) return UG_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (n == 0 || nsteps == 0) {

@@ -164,6 +164,7 @@ int ug_grid_build(const float *state_in, const uint32_t *perm_in, uint32_t n, fl
                   uint32_t max_boxes, ug_grid_info *info, void *ws, size_t ws_bytes,
                   int32_t *status, void *stream) {
     if (n == 0) return UG_OK;
+    if (n > kMaxAgents) return UG_EINVAL;
     if (!rows_ok(state_in) || !rows_ok(state_sorted) || !perm_sorted || !box_start || !info ||
         !status || !ws || !aligned(ws, 256) || !aligned(box_start, 16) || max_boxes < 27 || max_boxes > 0x7fffff00u ||
         !(contact_margin >= 0.0f))
@@ -190,6 +191,7 @@ int ug_grid_build(const float *state_in, const uint32_t *perm_in, uint32_t n, fl
 int ug_compute_forces(const float *state_sorted, const uint32_t *box_start, const ug_grid_info *info,
                       uint32_t n, ug_params p, float *force, int32_t *status, void *stream) {
     if (n == 0) return UG_OK;
+    if (n > kMaxAgents) return UG_EINVAL;
     if (!rows_ok(state_sorted) || !box_start || !info || !rows_ok(force) || !status) return UG_EINVAL;
     SimArgs sa{};
     sa.nsims = 1;
@@ -207,6 +209,7 @@ int ug_list_pairs(const float *state_sorted, const uint32_t *box_start, const ug
                   uint32_t n, float contact_margin, uint32_t max_per_agent, uint32_t *count,
                   uint32_t *nbr, int32_t *status, void *stream) {
     if (n == 0) return UG_OK;
+    if (n > kMaxAgents) return UG_EINVAL;
     if (!rows_ok(state_sorted) || !box_start || !info || !count || (!nbr && max_per_agent) ||
         !status)
         return UG_EINVAL;
@@ -227,6 +230,7 @@ int ug_list_pairs(const float *state_sorted, const uint32_t *box_start, const ug
 int ug_apply_displacement(const float *state_in, const float *force, uint32_t n, ug_params p,
                           float *state_out, float *disp_out, int32_t *status, void *stream) {
     if (n == 0) return UG_OK;
+    if (n > kMaxAgents) return UG_EINVAL;
     if (!rows_ok(state_in) || !rows_ok(force) || !rows_ok(state_out) ||
         (disp_out && !aligned(disp_out, 16)) || !status)
         return UG_EINVAL;
@@ -240,6 +244,7 @@ int ug_step(float *state, uint32_t *perm, uint32_t n, ug_params p, int32_t nstep
             uint32_t max_boxes, void *ws, size_t ws_bytes, int32_t *status, void *stream) {
     if (nsteps < 0) return UG_EINVAL;
     if (n == 0 || nsteps == 0) return UG_OK;
+    if (n > kMaxAgents) return UG_EINVAL;
     if (!rows_ok(state) || !perm || !status || !ws || !aligned(ws, 256) || max_boxes < 27 || max_boxes > 0x7fffff00u ||
         !(p.contact_margin >= 0.0f))
         return UG_EINVAL;
@@ -259,6 +264,7 @@ int ug_step_traced(float *state, uint32_t *perm, uint32_t n, ug_params p, int32_
                    void *const *events, int32_t nevents) {
     if (nsteps < 0 || !events || nevents < 2 + 5 * nsteps) return UG_EINVAL;
     if (n == 0 || nsteps == 0) return UG_OK;
+    if (n > kMaxAgents) return UG_EINVAL;
     if (!rows_ok(state) || !perm || !status || !ws || !aligned(ws, 256) || max_boxes < 27 || max_boxes > 0x7fffff00u ||
         !(p.contact_margin >= 0.0f))
         return UG_EINVAL;
@@ -280,6 +286,7 @@ int ug_step_batched(float *state, uint32_t *perm, const uint32_t *sim_offset, ui
                     void *stream) {
     if (nsteps < 0) return UG_EINVAL;
     if (n_total == 0 || nsteps == 0) return UG_OK;
+    if (n_total > kMaxAgents) return UG_EINVAL;
     if (!rows_ok(state) || !perm || !sim_offset || nsims == 0 || !params || !status || !ws ||
         !aligned(ws, 256) || max_boxes < 27)
         return UG_EINVAL;
@@ -306,6 +313,7 @@ int ug_tune_batched(const float *state, const uint32_t *sim_offset, uint32_t nsi
     best->sweep_block = 128;
     best->agents_per_lane = 2;
     if (n_total == 0) return UG_OK;
+    if (n_total > kMaxAgents) return UG_EINVAL;
     if (!rows_ok(state) || !sim_offset || nsims == 0 || !params || !ws || !aligned(ws, 256) ||
         max_boxes < 27)
         return UG_EINVAL;
@@ -386,6 +394,7 @@ int ug_forces_ladder(int32_t version, const float *state, uint32_t n, ug_params 
                      void *stream) {
     if (version < 0 || version > 3) return UG_EINVAL;
     if (n == 0) return UG_OK;
+    if (n > kMaxAgents) return UG_EINVAL;
     if (!rows_ok(state) || !force || !aligned(force, 16) || !status || !ws || !aligned(ws, 256) ||
         max_boxes < 27 || max_boxes > 0x7fffff00u || !(p.contact_margin >= 0.0f))
         return UG_EINVAL;
@@ -408,6 +417,7 @@ int ug_forces_ladder(int32_t version, const float *state, uint32_t n, ug_params 
 
 int ug_iota(uint32_t *perm, uint32_t n, void *stream) {
     if (n == 0) return UG_OK;
+    if (n > kMaxAgents) return UG_EINVAL;
     if (!perm) return UG_EINVAL;
     k_iota<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(perm, n);
     return last_launch();
@@ -416,6 +426,7 @@ int ug_iota(uint32_t *perm, uint32_t n, void *stream) {
 int ug_scatter_rows(const float *rows, const uint32_t *perm, uint32_t n, float *rows_by_id,
                     void *stream) {
     if (n == 0) return UG_OK;
+    if (n > kMaxAgents) return UG_EINVAL;
     if (!rows_ok(rows) || !perm || !rows_ok(rows_by_id)) return UG_EINVAL;
     k_scatter_rows<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
         reinterpret_cast<const float4 *>(rows), perm, n, reinterpret_cast<float4 *>(rows_by_id));
@@ -425,6 +436,7 @@ int ug_scatter_rows(const float *rows, const uint32_t *perm, uint32_t n, float *
 int ug_gather_rows(const float *rows_by_id, const uint32_t *perm, uint32_t n, float *rows,
                    void *stream) {
     if (n == 0) return UG_OK;
+    if (n > kMaxAgents) return UG_EINVAL;
     if (!rows_ok(rows_by_id) || !perm || !rows_ok(rows)) return UG_EINVAL;
     k_gather_rows<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
         reinterpret_cast<const float4 *>(rows_by_id), perm, n, reinterpret_cast<float4 *>(rows));

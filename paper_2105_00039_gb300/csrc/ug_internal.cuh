@@ -22,6 +22,7 @@ static_assert(kScanTile == 1 << kScanTileShift, "scan tile must be 2^kScanTileSh
 // L2 lines instead of queueing on one per tile.
 constexpr uint32_t kTileSumStride = 32;
 constexpr uint32_t kTileCopies = 8;
+constexpr uint32_t kMaxAgents = 1u << 30;               // largest n any entry point accepts
 constexpr int kBoundsWords = 8;                         // per simulation, see bounds_*()
 constexpr int kBoundsCopiesSingle = 32;                 // spread atomics when nsims == 1
 

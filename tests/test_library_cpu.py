@@ -115,3 +115,15 @@ def test_ladder_validation_without_device(lib):
     assert lib.ug_forces_ladder(1, None, 10, p, 100, fake, fake, 1 << 30, fake, None) == -1
     assert lib.ug_forces_ladder(2, fake, 10, p, 10, fake, fake, 1 << 30, fake, None) == -1
     assert lib.ug_forces_ladder(3, fake, 1000, p, 5000, fake, fake, need - 1, fake, None) == -5
+
+
+def test_agent_count_limit_without_device(lib):
+    P = ctypes.c_void_p
+    lib.ug_step.argtypes = [P, P, ctypes.c_uint32, _Params, ctypes.c_int32, ctypes.c_uint32, P,
+                            ctypes.c_size_t, P, P]
+    p = _Params(2, 1, 0.1, 1, 0.02, 3, 0)
+    fake = ctypes.c_void_p(0x10000)
+    too_many = (1 << 30) + 1
+    assert lib.ug_step(fake, fake, too_many, p, 1, 100, fake, 1 << 62, fake, None) == -1
+    lib.ug_iota.argtypes = [P, ctypes.c_uint32, P]
+    assert lib.ug_iota(fake, too_many, None) == -1
