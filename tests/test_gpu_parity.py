@@ -457,11 +457,26 @@ def test_density_sweep_4m_sampled(U, nbar):
     assert 0.6 * nbar < nb < 1.2 * nbar
 
 
-def test_dense_grid_step(U):
-    """A dense population (about 24 agents per box, ~60 neighbours per agent):
-    one fused step against the oracle, and three steps bit for bit against the
-    one-agent-per-lane sweep of the batched entry."""
-    st = P.density_cube(20000, 60.0, seed=31)
+def _thin_slab(n, thickness, side, seed):
+    """Uniform centres in [0, thickness] x [0, side]^2, diameters U[8, 12]:
+    a grid only 3 or 4 boxes wide in x, where most pairs of consecutive agents
+    must not share a merged run."""
+    st = P.uniform_cube(n, side, 8.0, 12.0, seed)
+    st[:, 0] = st[:, 0] * np.float32(thickness / side)
+    return st
+
+
+@pytest.mark.parametrize("name", ["dense", "slab_x3", "slab_x4"])
+def test_step_against_oracle_and_one_agent_kernel(U, name):
+    """Dense grids (about 24 agents per box, ~60 neighbours) and grids 3 or 4
+    boxes wide in x: one fused step against the oracle, and three steps bit for
+    bit against the one-agent-per-lane sweep of the batched entry."""
+    st = {"dense": lambda: P.density_cube(20000, 60.0, seed=31),
+          "slab_x3": lambda: _thin_slab(6000, 5.0, 600.0, 32),
+          "slab_x4": lambda: _thin_slab(6000, 14.0, 600.0, 33)}[name]()
+    if name != "dense":
+        g = O.grid(st)
+        assert g["dims"][0] == (3 if name == "slab_x3" else 4)
     prm = O.Params()
     out, perm = _run_steps(U, st, U.Params(), 1)
     newg = by_id(out.astype(np.float64), perm)
@@ -472,6 +487,7 @@ def test_dense_grid_step(U):
     ok = dp <= ulp32(newg[:, :3]) + TOL_STEP * np.maximum(np.linalg.norm(ref["u"], axis=1),
                                                           scale)[:, None]
     assert ok[~flips].all()
+    assert ref["npairs"].mean() > 2.0
     # three steps: two agents per lane (plain) == one agent per lane (batched, 1 simulation)
     a, pa = _run_steps(U, st, U.Params(), 3)
     x = _gpu(st)
