@@ -134,12 +134,14 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
         c1 = 0;
     };
     // One lockstep walk over candidates [0, len) of this lane, candidate t being
-    // row index_of(t) (t clamped into the lane's range, masked when t >= len).
+    // row index_of(t) (t clamped into the lane's range, masked when t >= len);
+    // four candidates per iteration keep four row loads in flight per lane.
+    constexpr int kWalkUnroll = 4;
     auto walk = [&](int len, int lmax, bool s0, bool s1, auto index_of) {
         const int last = max(len - 1, 0);
-        for (int t = 0; t < lmax; t += kSweepUnroll) {
+        for (int t = 0; t < lmax; t += kWalkUnroll) {
 #pragma unroll
-            for (int u = 0; u < kSweepUnroll; ++u) {
+            for (int u = 0; u < kWalkUnroll; ++u) {
                 const uint32_t jc = index_of(min(t + u, last));
                 const float4 q = __ldg(st + jc);
                 const bool in = t + u < len;
@@ -152,7 +154,7 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
                     ++c1;
                 }
             }
-            if (__any_sync(kFull, max(c0, c1) > kListCap2 - kSweepUnroll)) flush();
+            if (__any_sync(kFull, max(c0, c1) > kListCap2 - kWalkUnroll)) flush();
         }
     };
     // The 9 runs come as 3 neighbour planes (dz) of 3 runs (dy = -1, 0, +1),
