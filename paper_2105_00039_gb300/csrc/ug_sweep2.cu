@@ -290,6 +290,7 @@ k_sweep2m(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
         c0 = 0;
         c1 = 0;
     };
+    constexpr int kWalkUnroll = 4;   // candidates per walk iteration (row loads in flight per lane)
     const int nruns = __any_sync(kFull, split) ? 18 : 9;
 #pragma unroll 1
     for (int r = 0; r < nruns; ++r) {
@@ -311,9 +312,9 @@ k_sweep2m(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
         }
         const int last = max(len - 1, 0);
         const int lmax = (int)__reduce_max_sync(kFull, (unsigned)len);
-        for (int t = 0; t < lmax; t += kSweepUnroll) {
+        for (int t = 0; t < lmax; t += kWalkUnroll) {
 #pragma unroll
-            for (int u = 0; u < kSweepUnroll; ++u) {
+            for (int u = 0; u < kWalkUnroll; ++u) {
                 const uint32_t jc = b + (uint32_t)min(t + u, last);
                 const float4 q = __ldg(st + jc);
                 const bool in = t + u < len;
@@ -326,7 +327,7 @@ k_sweep2m(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
                     ++c1;
                 }
             }
-            if (__any_sync(kFull, max(c0, c1) > kListCap2 - kSweepUnroll)) flush();
+            if (__any_sync(kFull, max(c0, c1) > kListCap2 - kWalkUnroll)) flush();
         }
     }
     flush();
