@@ -317,7 +317,7 @@ __device__ __forceinline__ bool prefilter(const float4 &q, const FilterRow &f) {
 // has no divergent branch.  Candidates passing the filter are handed to fn in
 // warp-converged batches so that the exact, expensive path never runs one lane
 // at a time.  All 32 lanes of every warp must call this.
-constexpr int kSweepUnroll = 2;
+constexpr int kSweepUnroll = 4;
 
 struct WarpLists {            // per-warp scratch of sweep_neighbours (shared memory)
     uint32_t lst[kListCap][32];
