@@ -1,6 +1,5 @@
 """The library's adjoint (ug_step_backward behind a torch.autograd.Function)
 against the FP64 oracle's adjoint and against FP64 central differences."""
-import os
 
 import numpy as np
 import pytest
@@ -118,9 +117,10 @@ def test_adjoint_lattice_along_gpu_trajectory(U):
     assert _nrel(dd, ref["ddiam"]) < TOL
 
 
-@pytest.mark.skipif(os.environ.get("UG_FULL_GRAD", "0") != "1",
-                    reason="full 262,144-cell gradient check takes minutes of oracle time")
 def test_adjoint_full_size_along_gpu_trajectory(U):
+    """The differentiable configuration at full size (64^3 cells, 50 steps,
+    checkpoints every 10): GPU gradients against the FP64 oracle adjoint along
+    the GPU's own trajectory (about a minute of oracle time)."""
     steps = 50
     st, target = _lattice_case(64, steps)
     L, dk, dg, dp, dd = _gpu_grad(U, st, target, U.Params(adherence=0.0), steps, 10)
