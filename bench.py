@@ -63,7 +63,7 @@ def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -663,9 +663,15 @@ def measure_density(dev, flush, reps=2, nsteps=20):
         names = ("key", "scan", "place", "canon", "sweep")
         split = {nm: sum(ev[1 + 5 * t + j].elapsed_time(ev[2 + 5 * t + j]) for t in range(nsteps))
                  * 1000.0 / nsteps for j, nm in enumerate(names)}
+        # the sweep against the FP32 ALU roof (the population is frozen: counts hold every step)
+        cand, cont = candidates_and_contacts(U, x0, prm)
+        flops = n * (FLOPS_PER_CANDIDATE * cand + FLOPS_PER_CONTACT * cont + FLOPS_PER_AGENT)
+        tflops = flops / (split["sweep"] * 1e-6) / 1e12
         rows.append({"n_agents": n, "mean_neighbours_target": nbar,
                      "agent_steps_per_s": n * nsteps / (ms / 1e3), "ms_per_step": per_step_s * 1e3,
                      "step_alg_gbs": alg / per_step_s / 1e9, "step_hbm_frac": alg / per_step_s / 1e9 / hbm,
+                     "candidates_per_agent": cand, "contacts_per_agent": cont,
+                     "sweep_alu_tflops": tflops, "sweep_alu_frac": tflops / FP32_PEAK_TFLOPS,
                      "kernel_us_per_step_traced": split})
         del x0, x, perm, sp
         torch.cuda.empty_cache()
