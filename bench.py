@@ -363,6 +363,7 @@ def run_ours(args, world, rank, local, pg):
         line["density_sweep"] = measure_density(dev, flush)
         line["version_ladder"] = measure_ladder(dev, flush)
         line["lattice_margin"] = measure_lattice_margin(dev, flush)
+        line["pairs_once"] = measure_pairs_once(dev, flush)
 
     if rank == 0 and not args.no_cpu_baseline:
         rate, secs = cpu_oracle_rate(st, 3)
@@ -565,6 +566,43 @@ def measure_lattice_margin(dev, flush, margin=1.5, nsteps=100, reps=2):
     return {"workload": f"lattice_1m with contact margin {margin}, {nsteps} fused steps",
             "agent_steps_per_s": n * nsteps / (ms / 1e3), "ms_per_step": ms / nsteps,
             "mean_neighbours_initial": float(F[:, 3].double().mean().item())}
+
+
+def measure_pairs_once(dev, flush, reps=5):
+    """Newton's third law (ug_forces_symmetric) on the box-sorted 2^20-cell
+    lattice: one force evaluation with every pair evaluated once (forward half
+    of each neighbourhood, fixed-point atomics to both agents), the same walk
+    over all 27 boxes, and the main path's force sweep (ug_compute_forces)."""
+    import torch
+
+    from paper_2105_00039_gb300 import populations as P
+    from paper_2105_00039_gb300 import ugmech as U
+    x = torch.from_numpy(P.lattice_1m(0)).to(dev)
+    n = x.shape[0]
+    prm = U.Params()
+    lib = U.load()
+    srt, perm, start, info, status = U.grid_build(x)
+    F = torch.empty_like(srt)
+    ws = U.workspace(32 * n + 256, dev)
+    out = {"workload": "2^20-cell lattice, box-sorted; one force evaluation (grid built beforehand)"}
+
+    def sym(once):
+        U._check(lib.ug_forces_symmetric(once, U._ptr(srt), U._ptr(start), U._ptr(info), n, prm.c(),
+                                         U._ptr(F), U._ptr(ws), ws.numel(), U._ptr(status),
+                                         U._stream()), "ug_forces_symmetric")
+
+    def main():
+        U._check(lib.ug_compute_forces(U._ptr(srt), U._ptr(start), U._ptr(info), n, prm.c(), U._ptr(F),
+                                       U._ptr(status), U._stream()), "ug_compute_forces")
+    for name, fn in (("pairs_once_fixed_point", lambda: sym(1)),
+                     ("pairs_from_both_sides_same_walk", lambda: sym(0)),
+                     ("main_path_force_sweep", main)):
+        fn()
+        U.check_status(status, name)
+        ms = _timed(fn, reps, flush)
+        U.check_status(status, name)
+        out[name] = {"ms": ms, "agents_per_s": n / (ms / 1e3)}
+    return out
 
 
 def measure_ladder(dev, flush, reps=3):

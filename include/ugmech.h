@@ -277,6 +277,25 @@ int ug_forces_ladder(int32_t version, const float *state, uint32_t n, ug_params 
                      uint32_t max_boxes, double *force, void *ws, size_t ws_bytes, int32_t *status,
                      void *stream);
 
+/* ------------------------------------------------------------------ symmetric pairs */
+
+/* Symmetric (Newton's third law) evaluation of Eq. 1, for comparison with the
+ * main path only.  Same inputs and output layout as ug_compute_forces (rows,
+ * box table and grid record of ug_grid_build; force[n] = (Fx, Fy, Fz,
+ * overlapping pairs) per sorted row).  each_pair_once != 0: every agent walks
+ * only the forward half of its neighbourhood (the plane above, the row above,
+ * the rest of its own run), so each overlapping pair is evaluated once and its
+ * force is added to both agents; 0: every agent walks all 27 boxes.  Sums are
+ * accumulated as 64-bit fixed point (units of 2^-32) with integer atomics, so
+ * both modes are deterministic and give the same bits; the float-float contact
+ * test and Eq. 1 are the main path's, summed in fixed point rather than with
+ * compensated float32 sums.  A force component of 2^30 or more records
+ * UG_EBADSTATE.
+ *   ws  >= 32 * n bytes, 256-B aligned (the fixed-point accumulators) */
+int ug_forces_symmetric(int32_t each_pair_once, const float *state_sorted, const uint32_t *box_start,
+                        const ug_grid_info *info, uint32_t n, ug_params p, float *force, void *ws,
+                        size_t ws_bytes, int32_t *status, void *stream);
+
 /* ------------------------------------------------------------------ helpers */
 
 /* perm[i] = i. */

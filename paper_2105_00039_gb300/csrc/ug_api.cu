@@ -415,6 +415,20 @@ int ug_forces_ladder(int32_t version, const float *state, uint32_t n, ug_params 
                       next, force, status, s);
 }
 
+int ug_forces_symmetric(int32_t each_pair_once, const float *state_sorted, const uint32_t *box_start,
+                        const ug_grid_info *info, uint32_t n, ug_params p, float *force, void *ws,
+                        size_t ws_bytes, int32_t *status, void *stream) {
+    if (n == 0) return UG_OK;
+    if (n > kMaxAgents) return UG_EINVAL;
+    if (!rows_ok(state_sorted) || !box_start || !info || !rows_ok(force) || !status || !ws ||
+        !aligned(ws, 256))
+        return UG_EINVAL;
+    if (ws_bytes < 32 * (size_t)n) return UG_EWORKSPACE;
+    return run_symmetric(each_pair_once != 0, reinterpret_cast<const float4 *>(state_sorted), box_start,
+                         info, n, p, static_cast<unsigned long long *>(ws),
+                         reinterpret_cast<float4 *>(force), status, static_cast<cudaStream_t>(stream));
+}
+
 int ug_iota(uint32_t *perm, uint32_t n, void *stream) {
     if (n == 0) return UG_OK;
     if (n > kMaxAgents) return UG_EINVAL;

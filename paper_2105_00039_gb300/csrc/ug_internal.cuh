@@ -606,6 +606,11 @@ struct Workspace {
 };
 
 size_t layout_workspace(void *base, uint32_t n, uint32_t nsims, uint32_t max_boxes, Workspace *w);
+// Symmetric pair evaluation (ug_symmetric.cu): forces of box-sorted rows with
+// each pair evaluated once (forward) or from both sides, acc[4n] int64 scratch.
+int run_symmetric(bool forward, const float4 *sorted, const uint32_t *start, const ug_grid_info *geo,
+                  uint32_t n, const ug_params &p, unsigned long long *acc, float4 *force,
+                  int32_t *status, cudaStream_t s);
 // The paper's version ladder (ug_ladder.cu): forces of `state` (caller's order)
 // into force[4n] float64, with head[max_boxes] and next[n] as scratch.
 int run_ladder(int version, const float4 *state, uint32_t n, const SimArgs &sa, uint32_t max_boxes,

@@ -1,0 +1,157 @@
+// Symmetric pair evaluation (Newton's third law) of Eq. 1, for comparison with
+// the main path only; the step never uses it.
+//
+// Each agent walks only the forward half of its neighbourhood -- the three runs
+// of the plane above (dz = +1), the run of the row above in its own plane
+// (dz = 0, dy = +1), and the rest of its own run (the later agents of its box
+// and the box after it) -- so every overlapping pair is found once, by its
+// earlier agent.  The pair's force goes to both agents as 64-bit fixed-point
+// integers (2^-32 units): integer sums do not depend on the order of the
+// atomics, so the result is deterministic.  The same kernel with FORWARD =
+// false walks all 27 boxes and adds only to its own agent, which gives the
+// same bits (f_ji = -f_ij exactly in the float-float contact arithmetic, and
+// rounding to fixed point is symmetric): the comparison that isolates what
+// evaluating each pair once saves.
+#include <cuda_runtime.h>
+
+#include "ug_internal.cuh"
+
+namespace ug {
+
+constexpr float kFixScale = 4294967296.0f;           // 2^32
+constexpr float kFixLimit = 1073741824.0f;            // |force component| < 2^30
+
+__device__ __forceinline__ long long to_fix(float v) { return __float2ll_rn(v * kFixScale); }
+
+template <bool FORWARD>
+__global__ void __launch_bounds__(128)
+k_sym(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
+      const ug_grid_info *__restrict__ geo, uint32_t n, ug_params P,
+      unsigned long long *acc, int32_t *status) {
+    __shared__ WarpLists wl[4];
+    if (cta_failed(status)) return;
+    const int lane = threadIdx.x & 31;
+    WarpLists &w = wl[threadIdx.x >> 5];
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < n;
+    const ug_grid_info g = geo[0];
+    const float m2 = 2.0f * P.contact_margin;
+    const float4 me = valid ? __ldg(st + i) : make_float4(1e30f, 1e30f, 1e30f, 1.0f);
+    uint32_t key = 0;
+    if (valid) {
+        int bx, by, bz;
+        key = box_key(me, g, bx, by, bz);
+    }
+    const bool exact_diffs = __all_sync(kFull, !valid || far_from_origin(me, g.edge));
+    const FilterRow fr = make_filter_row(me, m2);
+    const float ri = 0.5f * me.w;
+    const int row = g.dims[0], plane = g.dims[0] * g.dims[1];
+    long long sx = 0, sy = 0, sz = 0;
+    uint32_t np = 0;
+    bool overflow = false;
+    int cnt = 0;
+    auto flush = [&]() {
+        const int m = (int)__reduce_max_sync(kFull, (unsigned)cnt);
+        for (int k = 0; k < m; ++k) {
+            if (k >= cnt) continue;
+            const uint32_t j = w.lst[k][lane];
+            ContactGeo c;
+            const float4 q = __ldg(st + j);
+            const bool hit = exact_diffs ? contact_t<false>(me, ri, q, m2, c)
+                                         : contact_t<true>(me, ri, q, m2, c);
+            if (!hit) continue;
+            const float coef = eq1_coef(ri, c.rb, c.rsum, c.delta, c.invd, P.k, P.gamma);
+            const float fx = __fmul_rn(coef, c.hx), fy = __fmul_rn(coef, c.hy), fz = __fmul_rn(coef, c.hz);
+            overflow |= !(fabsf(fx) < kFixLimit && fabsf(fy) < kFixLimit && fabsf(fz) < kFixLimit);
+            const long long ax = to_fix(fx), ay = to_fix(fy), az = to_fix(fz);
+            sx += ax;
+            sy += ay;
+            sz += az;
+            ++np;
+            if (FORWARD) {   // Newton's third law: the same pair pushes j the other way
+                atomicAdd(acc + 4 * (size_t)j + 0, (unsigned long long)(-ax));
+                atomicAdd(acc + 4 * (size_t)j + 1, (unsigned long long)(-ay));
+                atomicAdd(acc + 4 * (size_t)j + 2, (unsigned long long)(-az));
+                atomicAdd(acc + 4 * (size_t)j + 3, 1ull);
+            }
+        }
+        cnt = 0;
+    };
+    // runs: FORWARD walks (dz = +1, dy = -1..1), (dz = 0, dy = +1) and the own
+    // run after i; otherwise all 9 runs
+    constexpr int kRuns = FORWARD ? 5 : 9;
+#pragma unroll 1
+    for (int r = 0; r < kRuns; ++r) {
+        uint32_t b = valid ? i : 0u;
+        int len = 0;
+        if (valid) {
+            if (FORWARD && r == 4) {
+                b = i + 1;
+                len = (int)(__ldg(start + key + 2) - b);
+            } else {
+                const int dz = FORWARD ? (r < 3 ? 1 : 0) : r / 3 - 1;
+                const int dy = FORWARD ? (r < 3 ? r - 1 : 1) : r % 3 - 1;
+                const uint32_t kb = (uint32_t)((int)key + dz * plane + dy * row);
+                b = __ldg(start + kb - 1);
+                len = (int)(__ldg(start + kb + 2) - b);
+            }
+            if (len <= 0) { len = 0; b = i; }
+        }
+        const int last = max(len - 1, 0);
+        const int lmax = (int)__reduce_max_sync(kFull, (unsigned)len);
+        for (int t = 0; t < lmax; t += kSweepUnroll) {
+#pragma unroll
+            for (int u = 0; u < kSweepUnroll; ++u) {
+                const uint32_t jc = b + (uint32_t)min(t + u, last);
+                const float4 q = __ldg(st + jc);
+                if ((t + u < len) & (jc != i) & prefilter(q, fr)) {
+                    w.lst[cnt][lane] = jc;
+                    ++cnt;
+                }
+            }
+            if (__any_sync(kFull, cnt > kListCap - kSweepUnroll)) flush();
+        }
+    }
+    flush();
+    if (overflow) set_status(status, UG_EBADSTATE);
+    if (!valid) return;
+    if (FORWARD) {
+        atomicAdd(acc + 4 * (size_t)i + 0, (unsigned long long)sx);
+        atomicAdd(acc + 4 * (size_t)i + 1, (unsigned long long)sy);
+        atomicAdd(acc + 4 * (size_t)i + 2, (unsigned long long)sz);
+        atomicAdd(acc + 4 * (size_t)i + 3, (unsigned long long)np);
+    } else {
+        acc[4 * (size_t)i + 0] = (unsigned long long)sx;
+        acc[4 * (size_t)i + 1] = (unsigned long long)sy;
+        acc[4 * (size_t)i + 2] = (unsigned long long)sz;
+        acc[4 * (size_t)i + 3] = (unsigned long long)np;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_sym_finish(const unsigned long long *__restrict__ acc, uint32_t n, float4 *__restrict__ force,
+             int32_t *status) {
+    if (cta_failed(status)) return;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float inv = 1.0f / kFixScale;
+    force[i] = make_float4((float)(long long)acc[4 * (size_t)i + 0] * inv,
+                           (float)(long long)acc[4 * (size_t)i + 1] * inv,
+                           (float)(long long)acc[4 * (size_t)i + 2] * inv,
+                           (float)acc[4 * (size_t)i + 3]);
+}
+
+int run_symmetric(bool forward, const float4 *sorted, const uint32_t *start, const ug_grid_info *geo,
+                  uint32_t n, const ug_params &p, unsigned long long *acc, float4 *force,
+                  int32_t *status, cudaStream_t s) {
+    if (forward && cudaMemsetAsync(acc, 0, 32 * (size_t)n, s) != cudaSuccess) return UG_ECUDA;
+    const unsigned grid = (unsigned)((n + 127) / 128);
+    if (forward)
+        k_sym<true><<<grid, 128, 0, s>>>(sorted, start, geo, n, p, acc, status);
+    else
+        k_sym<false><<<grid, 128, 0, s>>>(sorted, start, geo, n, p, acc, status);
+    k_sym_finish<<<(n + 255) / 256, 256, 0, s>>>(acc, n, force, status);
+    return cudaGetLastError() == cudaSuccess ? UG_OK : UG_ECUDA;
+}
+
+}  // namespace ug

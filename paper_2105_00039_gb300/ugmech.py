@@ -29,7 +29,8 @@ EXPORTED = ("ug_strerror", "ug_version", "ug_workspace_bytes", "ug_grid_build",
             "ug_step_traced",
             "ug_step_batched", "ug_tune_batched", "ug_backward_workspace_bytes",
             "ug_step_backward", "ug_iota", "ug_scatter_rows", "ug_gather_rows",
-            "ug_grid_build_noalloc", "ug_ladder_workspace_bytes", "ug_forces_ladder")
+            "ug_grid_build_noalloc", "ug_ladder_workspace_bytes", "ug_forces_ladder",
+            "ug_forces_symmetric")
 
 
 class UgError(RuntimeError):
@@ -104,6 +105,8 @@ _SIG = {
                                         _P, ctypes.c_size_t, _P, _P]),
     "ug_iota": (ctypes.c_int, [_P, _U32, _P]),
     "ug_ladder_workspace_bytes": (ctypes.c_size_t, [_U32, _U32]),
+    "ug_forces_symmetric": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _U32, ug_params, _P, _P,
+                                           ctypes.c_size_t, _P, _P]),
     "ug_forces_ladder": (ctypes.c_int, [ctypes.c_int32, _P, _U32, ug_params, _U32, _P, _P,
                                         ctypes.c_size_t, _P, _P]),
     "ug_scatter_rows": (ctypes.c_int, [_P, _P, _U32, _P, _P]),
@@ -275,6 +278,26 @@ def list_pairs(state_sorted, box_start, info, contact_margin: float = 0.0,
     if check:
         check_status(status, "ug_list_pairs")
     return count, nbr
+
+
+def forces_symmetric(state_sorted, box_start, info, params: Params = Params(),
+                     each_pair_once: bool = True, status=None, check: bool = True) -> torch.Tensor:
+    """(Fx, Fy, Fz, contacts) per sorted row with Newton's third law: each pair
+    evaluated once and added to both agents (fixed-point sums), or from both
+    sides when each_pair_once is False (same bits)."""
+    lib = load()
+    _rows(state_sorted, "state_sorted")
+    n = state_sorted.shape[0]
+    force = torch.empty_like(state_sorted)
+    ws = workspace(32 * n + 256, state_sorted.device)
+    status = new_status(state_sorted.device) if status is None else status
+    rc = lib.ug_forces_symmetric(int(bool(each_pair_once)), _ptr(state_sorted), _ptr(box_start),
+                                 _ptr(info), n, params.c(), _ptr(force), _ptr(ws), ws.numel(),
+                                 _ptr(status), _stream())
+    _check(rc, "ug_forces_symmetric")
+    if check:
+        check_status(status, "ug_forces_symmetric")
+    return force
 
 
 def forces_ladder(state, version: int, params: Params = Params(), max_boxes: int | None = None,
