@@ -197,6 +197,18 @@ int ug_apply_displacement(const float *state_in, const float *force, uint32_t n,
 int ug_step(float *state, uint32_t *perm, uint32_t n, ug_params p, int32_t nsteps,
             uint32_t max_boxes, void *ws, size_t ws_bytes, int32_t *status, void *stream);
 
+/* ug_step with every overlapping pair evaluated once (Newton's third law): each
+ * agent walks only the forward half of its neighbourhood and the pair's force
+ * is added to both agents as 64-bit fixed point (units of 2^-32, integer
+ * atomics, so still deterministic), after which a second kernel moves the
+ * agents.  Same arguments, workspace and results within the same tolerance as
+ * ug_step, but not the same bits (fixed-point instead of compensated float32
+ * sums).  It pays in dense grids: 1.6x at ~32 and 1.8x at ~64 neighbours per
+ * agent on GB300, while on sparse grids (a few agents per box) the atomics cost
+ * more than the halved walk saves and ug_step is faster.  Single simulation. */
+int ug_step_pairs_once(float *state, uint32_t *perm, uint32_t n, ug_params p, int32_t nsteps,
+                       uint32_t max_boxes, void *ws, size_t ws_bytes, int32_t *status, void *stream);
+
 /* ug_step with CUDA events recorded between its kernels, for per-kernel timing.
  *   events  HOST array of nevents cudaEvent_t handles created by the caller
  *   nevents >= 2 + 5 * nsteps.  events[0] precedes the bounding-box kernel;
@@ -279,8 +291,8 @@ int ug_forces_ladder(int32_t version, const float *state, uint32_t n, ug_params 
 
 /* ------------------------------------------------------------------ symmetric pairs */
 
-/* Symmetric (Newton's third law) evaluation of Eq. 1, for comparison with the
- * main path only.  Same inputs and output layout as ug_compute_forces (rows,
+/* Symmetric (Newton's third law) evaluation of Eq. 1 (the force evaluation of
+ * ug_step_pairs_once).  Same inputs and output layout as ug_compute_forces (rows,
  * box table and grid record of ug_grid_build; force[n] = (Fx, Fy, Fz,
  * overlapping pairs) per sorted row).  each_pair_once != 0: every agent walks
  * only the forward half of its neighbourhood (the plane above, the row above,

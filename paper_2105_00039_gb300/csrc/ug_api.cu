@@ -27,8 +27,9 @@ int device_sm_count() {
 
 static uint32_t bounds_copies(uint32_t nsims) { return nsims == 1 ? kBoundsCopiesSingle : 1u; }
 
-// Layout (base may be null to size only).  The first four regions (ctrl, tile
-// sums, counts, bounds) are contiguous and are the only ones that need zeroing.
+// Layout (base may be null to size only).  The first five regions (ctrl, tile
+// sums, counts, bounds, fixed-point force sums) are contiguous and are the only
+// ones that need zeroing.
 size_t layout_workspace(void *base, uint32_t n, uint32_t nsims, uint32_t max_boxes, Workspace *w) {
     size_t off = 0;
     char *b = static_cast<char *>(base);
@@ -43,6 +44,7 @@ size_t layout_workspace(void *base, uint32_t n, uint32_t nsims, uint32_t max_box
     w->counts = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (size_t)max_boxes));
     w->bounds = reinterpret_cast<uint32_t *>(
         take(sizeof(uint32_t) * kBoundsWords * (size_t)bounds_copies(nsims) * nsims));
+    w->acc = reinterpret_cast<unsigned long long *>(take(32 * (size_t)n));
     const size_t zero_end = off;
     w->start = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * ((size_t)max_boxes + 1)));
     w->key = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (size_t)n));
@@ -97,7 +99,9 @@ int run_steps(float4 *state, uint32_t *perm, const SimArgs &sa, int nsteps, uint
         o.geo_next = w.geo;
         o.ctrl = w.ctrl;
         o.max_boxes = max_boxes;
-        if (agents_per_lane == 2)
+        if (agents_per_lane == 3)
+            launch_sym_step(sorted, start, w.geo, sa, o, w.acc, status, s, w.rank);
+        else if (agents_per_lane == 2)
             launch_sweep2(kSweepStep, sorted, start, w.geo, sa, o, status, s, w.rank);
         else
             launch_sweep(kSweepStep, sorted, start, w.geo, sa, o, sweep_block, status, s, w.rank);
@@ -256,6 +260,25 @@ int ug_step(float *state, uint32_t *perm, uint32_t n, ug_params p, int32_t nstep
     sa.pval = p;
     sa.bounds_copies = bounds_copies(1);
     return run_steps(reinterpret_cast<float4 *>(state), perm, sa, nsteps, max_boxes, w, 128, 2,
+                     nullptr, status, static_cast<cudaStream_t>(stream));
+}
+
+int ug_step_pairs_once(float *state, uint32_t *perm, uint32_t n, ug_params p, int32_t nsteps,
+                       uint32_t max_boxes, void *ws, size_t ws_bytes, int32_t *status, void *stream) {
+    if (nsteps < 0) return UG_EINVAL;
+    if (n == 0 || nsteps == 0) return UG_OK;
+    if (n > kMaxAgents) return UG_EINVAL;
+    if (!rows_ok(state) || !perm || !status || !ws || !aligned(ws, 256) || max_boxes < 27 || max_boxes > 0x7fffff00u ||
+        !(p.contact_margin >= 0.0f))
+        return UG_EINVAL;
+    Workspace w;
+    if (layout_workspace(ws, n, 1, max_boxes, &w) > ws_bytes) return UG_EWORKSPACE;
+    SimArgs sa{};
+    sa.nsims = 1;
+    sa.n = n;
+    sa.pval = p;
+    sa.bounds_copies = bounds_copies(1);
+    return run_steps(reinterpret_cast<float4 *>(state), perm, sa, nsteps, max_boxes, w, 128, 3,
                      nullptr, status, static_cast<cudaStream_t>(stream));
 }
 

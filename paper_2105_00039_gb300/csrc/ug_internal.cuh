@@ -600,6 +600,7 @@ struct Workspace {
     ug_grid_info *geo;     // [nsims]
     uint32_t *bounds;      // [copies * nsims * 8]
     uint32_t *tile_sum;    // [ntiles * kTileCopies * kTileSumStride]  zero between steps
+    unsigned long long *acc;   // [n][4] fixed-point force sums of the symmetric step, zero between steps
     Ctrl *ctrl;
     uint32_t ntiles;
     size_t bytes;
@@ -648,6 +649,11 @@ struct SweepOut {
 void launch_sweep(int mode, const float4 *sorted, const uint32_t *start, const ug_grid_info *geo,
                   const SimArgs &sa, const SweepOut &out, int block, int32_t *status,
                   cudaStream_t s, const uint32_t *skey = nullptr);
+// Fused step with symmetric pair evaluation (ug_symmetric.cu): pairs once into
+// w.acc, then the move kernel (displacement, bounds, next grid) clears w.acc.
+void launch_sym_step(const float4 *sorted, const uint32_t *start, const ug_grid_info *geo,
+                     const SimArgs &sa, const SweepOut &out, unsigned long long *acc,
+                     int32_t *status, cudaStream_t s, const uint32_t *skey);
 // Two agents per lane (ug_sweep2.cu); single simulation, force or step mode.
 void launch_sweep2(int mode, const float4 *sorted, const uint32_t *start, const ug_grid_info *geo,
                    const SimArgs &sa, const SweepOut &out, int32_t *status, cudaStream_t s,

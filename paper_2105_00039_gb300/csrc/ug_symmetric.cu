@@ -1,5 +1,5 @@
-// Symmetric pair evaluation (Newton's third law) of Eq. 1, for comparison with
-// the main path only; the step never uses it.
+// Symmetric pair evaluation (Newton's third law) of Eq. 1: the force entry
+// ug_forces_symmetric and the step ug_step_pairs_once (k_sym + k_sym_move).
 //
 // Each agent walks only the forward half of its neighbourhood -- the three runs
 // of the plane above (dz = +1), the run of the row above in its own plane
@@ -23,12 +23,13 @@ constexpr float kFixLimit = 1073741824.0f;            // |force component| < 2^3
 
 __device__ __forceinline__ long long to_fix(float v) { return __float2ll_rn(v * kFixScale); }
 
-template <bool FORWARD>
+template <bool FORWARD, bool CHAINED>
 __global__ void __launch_bounds__(128)
 k_sym(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
       const ug_grid_info *__restrict__ geo, uint32_t n, ug_params P,
-      unsigned long long *acc, int32_t *status) {
+      unsigned long long *acc, int32_t *status, const uint32_t *__restrict__ skey) {
     __shared__ WarpLists wl[4];
+    if (CHAINED) chain_begin();
     if (cta_failed(status)) return;
     const int lane = threadIdx.x & 31;
     WarpLists &w = wl[threadIdx.x >> 5];
@@ -40,7 +41,7 @@ k_sym(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     uint32_t key = 0;
     if (valid) {
         int bx, by, bz;
-        key = box_key(me, g, bx, by, bz);
+        key = skey ? __ldg(skey + i) : box_key(me, g, bx, by, bz);
     }
     const bool exact_diffs = __all_sync(kFull, !valid || far_from_origin(me, g.edge));
     const FilterRow fr = make_filter_row(me, m2);
@@ -141,15 +142,62 @@ k_sym_finish(const unsigned long long *__restrict__ acc, uint32_t n, float4 *__r
                            (float)acc[4 * (size_t)i + 3]);
 }
 
+// Move kernel of the symmetric step: the fixed-point sums become F (and are
+// cleared for the next step), then the Sec. III displacement moves the agent,
+// the bounds of the moved rows accumulate, and the last CTA finalises the next
+// step's grid.
+__global__ void __launch_bounds__(256)
+k_sym_move(const float4 *__restrict__ st, unsigned long long *acc, SimArgs sa, SweepOut out,
+           int32_t *status) {
+    __shared__ uint32_t s_red[32 * kBoundsWords];
+    __shared__ FinalizeScratch fs;
+    chain_begin();
+    if (cta_failed(status)) return;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < sa.n;
+    const ug_params P = sa.pval;
+    uint32_t codes[8];
+    float4 nw = make_float4(0.f, 0.f, 0.f, 1.f);
+    if (valid) {
+        const float inv = 1.0f / kFixScale;
+        ulonglong2 *a2 = reinterpret_cast<ulonglong2 *>(acc + 4 * (size_t)i);
+        const ulonglong2 xy = a2[0], zc = a2[1];
+        a2[0] = make_ulonglong2(0ull, 0ull);
+        a2[1] = make_ulonglong2(0ull, 0ull);
+        const float Fx = (float)(long long)xy.x * inv, Fy = (float)(long long)xy.y * inv,
+                    Fz = (float)(long long)zc.x * inv;
+        const float4 me = __ldg(st + i);
+        bool mv, cp;
+        const float3 u = displacement(Fx, Fy, Fz, me.w, P, &mv, &cp);
+        nw = make_float4(me.x + u.x, me.y + u.y, me.z + u.z, me.w);
+        out.state_out[i] = nw;
+        if (out.force) out.force[i] = make_float4(Fx, Fy, Fz, (mv ? 1.f : 0.f) + (cp ? 2.f : 0.f));
+        if (!row_ok(nw)) set_status(status, UG_EBADSTATE);
+    }
+    bounds_codes(nw, valid, codes);
+    accumulate_bounds_codes(sa, codes, valid, 0u, true, out.bounds, s_red, kBoundsWords);
+    if (elect_last_cta(&out.ctrl->done))
+        finalize_grid(sa, out.bounds, out.geo_next, out.ctrl, out.max_boxes, status, fs);
+}
+
+void launch_sym_step(const float4 *sorted, const uint32_t *start, const ug_grid_info *geo,
+                     const SimArgs &sa, const SweepOut &out, unsigned long long *acc,
+                     int32_t *status, cudaStream_t s, const uint32_t *skey) {
+    const uint32_t n = sa.n;
+    launch_chained(k_sym<true, true>, (unsigned)((n + 127) / 128), 128u, s, sorted, start, geo, n,
+                   sa.pval, acc, status, skey);
+    launch_chained(k_sym_move, (unsigned)((n + 255) / 256), 256u, s, sorted, acc, sa, out, status);
+}
+
 int run_symmetric(bool forward, const float4 *sorted, const uint32_t *start, const ug_grid_info *geo,
                   uint32_t n, const ug_params &p, unsigned long long *acc, float4 *force,
                   int32_t *status, cudaStream_t s) {
     if (forward && cudaMemsetAsync(acc, 0, 32 * (size_t)n, s) != cudaSuccess) return UG_ECUDA;
     const unsigned grid = (unsigned)((n + 127) / 128);
     if (forward)
-        k_sym<true><<<grid, 128, 0, s>>>(sorted, start, geo, n, p, acc, status);
+        k_sym<true, false><<<grid, 128, 0, s>>>(sorted, start, geo, n, p, acc, status, nullptr);
     else
-        k_sym<false><<<grid, 128, 0, s>>>(sorted, start, geo, n, p, acc, status);
+        k_sym<false, false><<<grid, 128, 0, s>>>(sorted, start, geo, n, p, acc, status, nullptr);
     k_sym_finish<<<(n + 255) / 256, 256, 0, s>>>(acc, n, force, status);
     return cudaGetLastError() == cudaSuccess ? UG_OK : UG_ECUDA;
 }

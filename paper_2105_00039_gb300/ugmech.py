@@ -30,7 +30,7 @@ EXPORTED = ("ug_strerror", "ug_version", "ug_workspace_bytes", "ug_grid_build",
             "ug_step_batched", "ug_tune_batched", "ug_backward_workspace_bytes",
             "ug_step_backward", "ug_iota", "ug_scatter_rows", "ug_gather_rows",
             "ug_grid_build_noalloc", "ug_ladder_workspace_bytes", "ug_forces_ladder",
-            "ug_forces_symmetric")
+            "ug_forces_symmetric", "ug_step_pairs_once")
 
 
 class UgError(RuntimeError):
@@ -92,6 +92,8 @@ _SIG = {
     "ug_list_pairs": (ctypes.c_int, [_P, _P, _P, _U32, ctypes.c_float, _U32, _P, _P, _P, _P]),
     "ug_apply_displacement": (ctypes.c_int, [_P, _P, _U32, ug_params, _P, _P, _P, _P]),
     "ug_step": (ctypes.c_int, [_P, _P, _U32, ug_params, ctypes.c_int32, _U32, _P,
+                               ctypes.c_size_t, _P, _P]),
+    "ug_step_pairs_once": (ctypes.c_int, [_P, _P, _U32, ug_params, ctypes.c_int32, _U32, _P,
                                ctypes.c_size_t, _P, _P]),
     "ug_step_traced": (ctypes.c_int, [_P, _P, _U32, ug_params, ctypes.c_int32, _U32, _P,
                                       ctypes.c_size_t, _P, _P, ctypes.POINTER(ctypes.c_void_p),
@@ -350,13 +352,15 @@ class Stepper:
         self.ws = workspace(self.lib.ug_workspace_bytes(self.n, self.nsims, self.max_boxes), device)
         self.status = new_status(device)
 
-    def step(self, state, perm, params: Params, nsteps: int = 1):
+    def step(self, state, perm, params: Params, nsteps: int = 1, pairs_once: bool = False):
+        """nsteps fused steps; pairs_once selects ug_step_pairs_once (each pair
+        evaluated once, faster on dense grids)."""
         _rows(state, "state")
         _ids(perm, self.n, "perm")
-        rc = self.lib.ug_step(_ptr(state), _ptr(perm), self.n, params.c(), int(nsteps),
-                              self.max_boxes, _ptr(self.ws), self.ws.numel(), _ptr(self.status),
-                              _stream())
-        _check(rc, "ug_step")
+        fn = self.lib.ug_step_pairs_once if pairs_once else self.lib.ug_step
+        rc = fn(_ptr(state), _ptr(perm), self.n, params.c(), int(nsteps), self.max_boxes,
+                _ptr(self.ws), self.ws.numel(), _ptr(self.status), _stream())
+        _check(rc, "ug_step_pairs_once" if pairs_once else "ug_step")
 
     def step_traced(self, state, perm, params: Params, nsteps: int, events):
         """step() with caller-created torch.cuda.Event objects recorded between

@@ -150,23 +150,24 @@ def test_displacement_parity(U, name):
 
 
 # ------------------------------------------------------------------ fused step
-def _run_steps(U, st, prm, nsteps, max_boxes=None):
+def _run_steps(U, st, prm, nsteps, max_boxes=None, pairs_once=False):
     x = _gpu(st)
     n = len(st)
     if max_boxes is None:
         max_boxes = U.estimate_max_boxes(x, prm.contact_margin, slack=2.0)
     sp = U.Stepper(n, max_boxes, x.device)
     perm = U.iota(n, x.device)
-    sp.step(x, perm, prm, nsteps)
+    sp.step(x, perm, prm, nsteps, pairs_once=pairs_once)
     sp.check()
     return x.cpu().numpy(), perm.cpu().numpy()
 
 
+@pytest.mark.parametrize("pairs_once", [False, True])
 @pytest.mark.parametrize("name", list(workloads()))
-def test_fused_single_step(U, name):
+def test_fused_single_step(U, name, pairs_once):
     st, margin = workloads()[name]
     prm = O.Params(contact_margin=margin)
-    out, perm = _run_steps(U, st, U.Params(contact_margin=margin), 1)
+    out, perm = _run_steps(U, st, U.Params(contact_margin=margin), 1, pairs_once=pairs_once)
     g = O.grid(st, margin)
     assert np.array_equal(perm, g["perm"])          # rows come back in the step's box order
     newg = by_id(out.astype(np.float64), perm)
@@ -179,19 +180,21 @@ def test_fused_single_step(U, name):
     assert ok[~flips].all(), np.argwhere(~ok)[:5]
 
 
-def test_fused_step_is_deterministic(U):
+@pytest.mark.parametrize("pairs_once", [False, True])
+def test_fused_step_is_deterministic(U, pairs_once):
     st = P.uniform_cube(20000, 250.0, 8.0, 12.0, 9)
-    a, pa = _run_steps(U, st, U.Params(), 5)
-    b, pb = _run_steps(U, st, U.Params(), 5)
+    a, pa = _run_steps(U, st, U.Params(), 5, pairs_once=pairs_once)
+    b, pb = _run_steps(U, st, U.Params(), 5, pairs_once=pairs_once)
     assert np.array_equal(a, b) and np.array_equal(pa, pb)
 
 
-def test_trajectory_100_steps(U):
+@pytest.mark.parametrize("pairs_once", [False, True])
+def test_trajectory_100_steps(U, pairs_once):
     """100 independent steps on both sides, no adherence threshold (the step is
     then continuous in the rows, so float32 and FP64 trajectories stay close)."""
     st = P.lattice_cube(16, seed=0)                    # 4096 cells, same recipe as the 1M lattice
     prm = O.Params(adherence=0.0)
-    out, perm = _run_steps(U, st, U.Params(adherence=0.0), 100)
+    out, perm = _run_steps(U, st, U.Params(adherence=0.0), 100, pairs_once=pairs_once)
     final_g = by_id(out.astype(np.float64), perm)[:, :3]
     final_r, recs = O.trajectory(st, prm, 100, keep=True)
     mean_u = np.mean([np.linalg.norm(r["u"], axis=1).mean() for r in recs])
@@ -499,3 +502,27 @@ def test_step_against_oracle_and_one_agent_kernel(U, name):
                     U.Params().as_tensor(DEV)[None], 3, t)
     sp.check("batched-1")
     assert np.array_equal(a, x.cpu().numpy()) and np.array_equal(pa, pb.cpu().numpy())
+
+
+@pytest.mark.parametrize("name", ["dense", "slab_x3", "slab_x4"])
+def test_pairs_once_step_against_oracle(U, name):
+    """ug_step_pairs_once on a dense grid and on grids 3 or 4 boxes wide in x:
+    one step against the oracle, and three steps against the gather step
+    within the per-step tolerance of the displacements."""
+    st = {"dense": lambda: P.density_cube(20000, 60.0, seed=31),
+          "slab_x3": lambda: _thin_slab(6000, 5.0, 600.0, 32),
+          "slab_x4": lambda: _thin_slab(6000, 14.0, 600.0, 33)}[name]()
+    prm = O.Params()
+    out, perm = _run_steps(U, st, U.Params(), 1, pairs_once=True)
+    newg = by_id(out.astype(np.float64), perm)
+    ref = O.step(st, prm)
+    flips = adherence_flips(ref["Fn"], ref["S"], prm.adherence)
+    scale = ref["S"] / O.mass(st[:, 3].astype(np.float64), prm.as64())
+    dp = np.abs(newg[:, :3] - ref["state"][:, :3])
+    ok = dp <= ulp32(newg[:, :3]) + TOL_STEP * np.maximum(np.linalg.norm(ref["u"], axis=1),
+                                                          scale)[:, None]
+    assert ok[~flips].all()
+    a, pa = _run_steps(U, st, U.Params(adherence=0.0), 3, pairs_once=True)
+    b, pb = _run_steps(U, st, U.Params(adherence=0.0), 3)
+    ga, gb = by_id(a.astype(np.float64), pa), by_id(b.astype(np.float64), pb)
+    assert np.abs(ga[:, :3] - gb[:, :3]).max() < 1e-3
