@@ -319,6 +319,8 @@ def run_ours(args, world, rank, local, pg):
                      "traffic": sweep_traffic() if dom == "sweep" else None,
                      "avg_launch_us": avg_launch_ms * 1000.0,
                      "alg_flops_per_launch": alg_flops,
+                     "pairs_once_agent_steps_per_s": n * nsteps / (ms_once / 1e3),
+                     "pairs_once_ms_per_step": ms_once / nsteps,
                      "candidates_per_agent": cand, "contacts_per_agent": cont,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                      "note": "issue-bound: 74% of issue slots busy (ncu), see profiles/k_sweep2_lattice1m.md",
@@ -662,7 +664,8 @@ def measure_ladder(dev, flush, reps=3):
 def measure_density(dev, flush, reps=2, nsteps=20):
     """Benchmark-B style density sweep: uniform centres in cubes sized for a mean
     of 2, 8, 32, 64 overlapping neighbours (4,194,304 cells) and 12 (16,777,216
-    cells), max displacement 0 (frozen), 20 steps each."""
+    cells), max displacement 0 (frozen), 20 steps each, with ug_step and with
+    ug_step_pairs_once."""
     import torch
 
     from paper_2105_00039_gb300 import populations as P
@@ -681,13 +684,17 @@ def measure_density(dev, flush, reps=2, nsteps=20):
         x = torch.empty_like(x0)
         perm = torch.empty(n, dtype=torch.int32, device=dev)
 
-        def run():
+        def run(pairs_once=False):
             x.copy_(x0)
             U._check(lib.ug_iota(U._ptr(perm), n, U._stream()), "ug_iota")
-            sp.step(x, perm, prm, nsteps)
+            sp.step(x, perm, prm, nsteps, pairs_once=pairs_once)
         run(); sp.check("density"); torch.cuda.synchronize()
         ms = _timed(run, reps, flush)
         sp.check("density")
+        # the same steps with every pair evaluated once (ug_step_pairs_once)
+        run(True); sp.check("density, pairs once"); torch.cuda.synchronize()
+        ms_once = _timed(lambda: run(True), reps, flush)
+        sp.check("density, pairs once")
         per_step_s = ms / 1e3 / nsteps
         alg = BYTES_PER_AGENT_STEP * n + BYTES_PER_BOX * mb / 1.05
         # one traced pass for the per-kernel split (events un-chain the kernels)
@@ -708,6 +715,8 @@ def measure_density(dev, flush, reps=2, nsteps=20):
         rows.append({"n_agents": n, "mean_neighbours_target": nbar,
                      "agent_steps_per_s": n * nsteps / (ms / 1e3), "ms_per_step": per_step_s * 1e3,
                      "step_alg_gbs": alg / per_step_s / 1e9, "step_hbm_frac": alg / per_step_s / 1e9 / hbm,
+                     "pairs_once_agent_steps_per_s": n * nsteps / (ms_once / 1e3),
+                     "pairs_once_ms_per_step": ms_once / nsteps,
                      "candidates_per_agent": cand, "contacts_per_agent": cont,
                      "sweep_alu_tflops": tflops, "sweep_alu_frac": tflops / FP32_PEAK_TFLOPS,
                      "kernel_us_per_step_traced": split})
