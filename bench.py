@@ -415,7 +415,9 @@ def _timed(fn, reps, flush=None):
 def measure_batched(dev, flush, nsims=256, nsteps=50, reps=3):
     """256 independent simulations (agent counts log-uniform in [1e3, 2e5], mean
     neighbours U[4, 40]), 50 steps: the batched step captured as one CUDA graph
-    versus the 256 simulations run one after another with the plain step."""
+    versus the 256 simulations run one after another with the plain step of
+    the same method (ug_step, or ug_step_pairs_once when the tuner picks every
+    pair once)."""
     import torch
 
     from paper_2105_00039_gb300 import populations as P
@@ -471,7 +473,7 @@ def measure_batched(dev, flush, nsims=256, nsteps=50, reps=3):
         for k in range(nsims):
             xs[k].copy_(parts[k])
             U._check(lib.ug_iota(U._ptr(ps[k]), len(parts[k]), U._stream()), "ug_iota")
-            steppers[k].step(xs[k], ps[k], prm, nsteps)
+            steppers[k].step(xs[k], ps[k], prm, nsteps, pairs_once=bool(tune.pair_mode))
     sequential()
     torch.cuda.synchronize()
     t_seq = _timed(sequential, reps, flush)
@@ -484,7 +486,8 @@ def measure_batched(dev, flush, nsims=256, nsteps=50, reps=3):
             "sequential_agent_steps_per_s": n * nsteps / (t_seq / 1e3),
             "speedup": t_seq / t_batched, "bit_identical_to_plain": bool(same),
             "tuned_sweep_block": int(tune.sweep_block),
-            "tuned_agents_per_lane": int(tune.agents_per_lane)}
+            "tuned_agents_per_lane": int(tune.agents_per_lane),
+            "tuned_pair_mode": int(tune.pair_mode)}
 
 
 def measure_adjoint(dev, flush, side=64, nsteps=50, ckpt=10, reps=3):

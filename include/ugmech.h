@@ -104,11 +104,17 @@ typedef struct {
  *   agents_per_lane 2: each lane sweeps two box-sorted agents over their merged
  *                      neighbour runs (sweep_block is then fixed at 128);
  *                   1: one agent per lane with shared-memory staging, CTAs of
- *                      sweep_block threads.  0 = default (2). */
+ *                      sweep_block threads.  0 = default (2).
+ *   pair_mode       0: every agent sums its own pairs (as ug_step; default);
+ *                   1: every pair evaluated once (as ug_step_pairs_once; the
+ *                      two fields above are then ignored).  Either way a
+ *                      simulation's result is bit-identical to the matching
+ *                      single-simulation entry on its rows alone. */
 typedef struct {
     int32_t sweep_block;      /* 64 or 128; 0 = default (128) */
     int32_t agents_per_lane;  /* 1 or 2; 0 = default (2) */
-    int32_t reserved[6];
+    int32_t pair_mode;        /* 0 or 1; 0 = default */
+    int32_t reserved[5];
 } ug_tuning;
 
 /* ------------------------------------------------------------------ workspace */
@@ -205,7 +211,8 @@ int ug_step(float *state, uint32_t *perm, uint32_t n, ug_params p, int32_t nstep
  * ug_step, but not the same bits (fixed-point instead of compensated float32
  * sums).  It pays in dense grids: 1.6x at ~32 and 1.8x at ~64 neighbours per
  * agent on GB300, while on sparse grids (a few agents per box) the atomics cost
- * more than the halved walk saves and ug_step is faster.  Single simulation. */
+ * more than the halved walk saves and ug_step is faster.  For many simulations
+ * use ug_step_batched with tuning->pair_mode = 1. */
 int ug_step_pairs_once(float *state, uint32_t *perm, uint32_t n, ug_params p, int32_t nsteps,
                        uint32_t max_boxes, void *ws, size_t ws_bytes, int32_t *status, void *stream);
 
@@ -222,7 +229,8 @@ int ug_step_traced(float *state, uint32_t *perm, uint32_t n, ug_params p, int32_
 /* Many independent simulations advanced together (each kernel of a step covers
  * all of them; there is one grid per simulation).  Simulation s owns rows
  * sim_offset[s] .. sim_offset[s+1]-1 of state and perm and never mixes with
- * the others; its result is bit-identical to ug_step on its rows alone.
+ * the others; its result is bit-identical to ug_step (ug_step_pairs_once with
+ * tuning->pair_mode 1) on its rows alone.
  *   sim_offset [nsims + 1] DEVICE, non-decreasing, sim_offset[nsims] = n_total
  *   params     [nsims] DEVICE, per-simulation constants
  *   max_boxes  capacity of the shared box table (sum over simulations)
@@ -233,7 +241,7 @@ int ug_step_batched(float *state, uint32_t *perm, const uint32_t *sim_offset, ui
                     int32_t *status, void *stream);
 
 /* Time each candidate configuration (one agent per lane with 64 or 128 threads
- * per CTA, two agents per lane) on the given batched problem -- three fused
+ * per CTA, two agents per lane, every pair once) on the given batched problem -- three fused
  * steps (grid build, sweep, move) of a scratch copy of the rows, after one
  * untimed step -- and write the fastest to *best (HOST pointer).  `state` is
  * only read.  Needs ws_bytes >= ug_workspace_bytes(n_total, nsims, max_boxes)

@@ -323,7 +323,12 @@ int ug_step_batched(float *state, uint32_t *perm, const uint32_t *sim_offset, ui
     sa.bounds_copies = bounds_copies(nsims);
     const int block = tuning && tuning->sweep_block ? tuning->sweep_block : 128;
     const int apl = tuning && tuning->agents_per_lane ? tuning->agents_per_lane : 2;
-    if ((block != 64 && block != 128) || (apl != 1 && apl != 2)) return UG_EINVAL;
+    const int pair_mode = tuning ? tuning->pair_mode : 0;
+    if ((block != 64 && block != 128) || (apl != 1 && apl != 2) || (pair_mode != 0 && pair_mode != 1))
+        return UG_EINVAL;
+    if (pair_mode == 1)   // every pair once: its own kernels, whatever the sweep layout
+        return run_steps(reinterpret_cast<float4 *>(state), perm, sa, nsteps, max_boxes, w, 128, 3,
+                         nullptr, status, static_cast<cudaStream_t>(stream));
     return run_steps(reinterpret_cast<float4 *>(state), perm, sa, nsteps, max_boxes, w, block, apl,
                      nullptr, status, static_cast<cudaStream_t>(stream));
 }
@@ -369,14 +374,14 @@ int ug_tune_batched(const float *state, const uint32_t *sim_offset, uint32_t nsi
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return UG_ECUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return UG_ECUDA; }
-    // candidates: (agents per lane, threads per CTA), each timed on kTuneSteps
-    // fused steps (grid build + sweep + move) from the given rows, after one
-    // untimed step
+    // candidates: (agents per lane, threads per CTA), and every pair once (3),
+    // each timed on kTuneSteps fused steps (grid build + sweep + move) from the
+    // given rows, after one untimed step
     constexpr int kTuneSteps = 3;
-    const int cands[3][2] = {{1, 64}, {1, 128}, {2, 128}};
+    const int cands[4][2] = {{1, 64}, {1, 128}, {2, 128}, {3, 128}};
     float best_ms = 1e30f;
     int rc = UG_OK;
-    for (int c = 0; c < 3 && rc == UG_OK; ++c) {
+    for (int c = 0; c < 4 && rc == UG_OK; ++c) {
         rc = reset();
         if (rc == UG_OK)
             rc = run_steps(rows, ids, sa, 1, max_boxes, w, cands[c][1], cands[c][0], nullptr, status, s);
@@ -392,7 +397,8 @@ int ug_tune_batched(const float *state, const uint32_t *sim_offset, uint32_t nsi
         cudaEventElapsedTime(&ms, e0, e1);
         if (ms < best_ms) {
             best_ms = ms;
-            best->agents_per_lane = cands[c][0];
+            best->pair_mode = cands[c][0] == 3 ? 1 : 0;
+            best->agents_per_lane = cands[c][0] == 3 ? 2 : cands[c][0];
             best->sweep_block = cands[c][1];
         }
     }

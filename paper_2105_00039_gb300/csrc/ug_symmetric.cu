@@ -26,16 +26,22 @@ __device__ __forceinline__ long long to_fix(float v) { return __float2ll_rn(v * 
 template <bool FORWARD, bool CHAINED>
 __global__ void __launch_bounds__(128)
 k_sym(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
-      const ug_grid_info *__restrict__ geo, uint32_t n, ug_params P,
+      const ug_grid_info *__restrict__ geo, SimArgs sa,
       unsigned long long *acc, int32_t *status, const uint32_t *__restrict__ skey) {
     __shared__ WarpLists wl[4];
     if (CHAINED) chain_begin();
     if (cta_failed(status)) return;
     const int lane = threadIdx.x & 31;
     WarpLists &w = wl[threadIdx.x >> 5];
+    const uint32_t n = sa.n;
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < n;
-    const ug_grid_info g = geo[0];
+    // each lane with its own simulation's grid and constants (every pair lies
+    // inside one simulation, so the forward walk never leaves it)
+    bool uniform;
+    const uint32_t sim = cta_sim(sa, blockIdx.x * blockDim.x, i, uniform);
+    const ug_grid_info g = geo[sim];
+    const ug_params P = sim_params(sa, sim);
     const float m2 = 2.0f * P.contact_margin;
     const float4 me = valid ? __ldg(st + i) : make_float4(1e30f, 1e30f, 1e30f, 1.0f);
     uint32_t key = 0;
@@ -155,7 +161,9 @@ k_sym_move(const float4 *__restrict__ st, unsigned long long *acc, SimArgs sa, S
     if (cta_failed(status)) return;
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < sa.n;
-    const ug_params P = sa.pval;
+    bool uniform;
+    const uint32_t sim = cta_sim(sa, blockIdx.x * blockDim.x, i, uniform);
+    const ug_params P = sim_params(sa, sim);
     uint32_t codes[8];
     float4 nw = make_float4(0.f, 0.f, 0.f, 1.f);
     if (valid) {
@@ -175,7 +183,7 @@ k_sym_move(const float4 *__restrict__ st, unsigned long long *acc, SimArgs sa, S
         if (!row_ok(nw)) set_status(status, UG_EBADSTATE);
     }
     bounds_codes(nw, valid, codes);
-    accumulate_bounds_codes(sa, codes, valid, 0u, true, out.bounds, s_red, kBoundsWords);
+    accumulate_bounds_codes(sa, codes, valid, sim, uniform, out.bounds, s_red, kBoundsWords);
     if (elect_last_cta(&out.ctrl->done))
         finalize_grid(sa, out.bounds, out.geo_next, out.ctrl, out.max_boxes, status, fs);
 }
@@ -184,8 +192,8 @@ void launch_sym_step(const float4 *sorted, const uint32_t *start, const ug_grid_
                      const SimArgs &sa, const SweepOut &out, unsigned long long *acc,
                      int32_t *status, cudaStream_t s, const uint32_t *skey) {
     const uint32_t n = sa.n;
-    launch_chained(k_sym<true, true>, (unsigned)((n + 127) / 128), 128u, s, sorted, start, geo, n,
-                   sa.pval, acc, status, skey);
+    launch_chained(k_sym<true, true>, (unsigned)((n + 127) / 128), 128u, s, sorted, start, geo, sa,
+                   acc, status, skey);
     launch_chained(k_sym_move, (unsigned)((n + 255) / 256), 256u, s, sorted, acc, sa, out, status);
 }
 
@@ -193,11 +201,16 @@ int run_symmetric(bool forward, const float4 *sorted, const uint32_t *start, con
                   uint32_t n, const ug_params &p, unsigned long long *acc, float4 *force,
                   int32_t *status, cudaStream_t s) {
     if (forward && cudaMemsetAsync(acc, 0, 32 * (size_t)n, s) != cudaSuccess) return UG_ECUDA;
+    SimArgs sa{};
+    sa.nsims = 1;
+    sa.n = n;
+    sa.pval = p;
+    sa.bounds_copies = 1;
     const unsigned grid = (unsigned)((n + 127) / 128);
     if (forward)
-        k_sym<true, false><<<grid, 128, 0, s>>>(sorted, start, geo, n, p, acc, status, nullptr);
+        k_sym<true, false><<<grid, 128, 0, s>>>(sorted, start, geo, sa, acc, status, nullptr);
     else
-        k_sym<false, false><<<grid, 128, 0, s>>>(sorted, start, geo, n, p, acc, status, nullptr);
+        k_sym<false, false><<<grid, 128, 0, s>>>(sorted, start, geo, sa, acc, status, nullptr);
     k_sym_finish<<<(n + 255) / 256, 256, 0, s>>>(acc, n, force, status);
     return cudaGetLastError() == cudaSuccess ? UG_OK : UG_ECUDA;
 }

@@ -53,7 +53,7 @@ class ug_grid_info(ctypes.Structure):
 
 class ug_tuning(ctypes.Structure):
     _fields_ = [("sweep_block", ctypes.c_int32), ("agents_per_lane", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("pair_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 assert ctypes.sizeof(ug_grid_info) == 48

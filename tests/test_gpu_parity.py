@@ -257,7 +257,8 @@ def test_freeze_rule_max_disp_zero(U):
 
 
 # ------------------------------------------------------------------ batched
-def test_batched_bit_identical_to_plain(U):
+@pytest.mark.parametrize("pairs_once", [False, True])
+def test_batched_bit_identical_to_plain(U, pairs_once):
     rng_sizes = [1500, 37, 8000, 2600, 1, 12000, 640, 5000]
     parts = [P.density_cube(n, 4.0 + 6.0 * k, seed=100 + k) for k, n in enumerate(rng_sizes)]
     offs = np.zeros(len(parts) + 1, np.int64)
@@ -273,12 +274,14 @@ def test_batched_bit_identical_to_plain(U):
     perm = U.iota(n, x.device)
     off_t = torch.from_numpy(offs.astype(np.int32)).to(DEV)
     pdev = torch.stack([p.as_tensor(DEV) for p in params])
-    sp.step_batched(x, perm, off_t, pdev, nsteps=7)
+    t = U.ug_tuning()
+    t.pair_mode = 1 if pairs_once else 0
+    sp.step_batched(x, perm, off_t, pdev, nsteps=7, tuning=t)
     sp.check("batched")
     xb, pb = x.cpu().numpy(), perm.cpu().numpy()
     for k, part in enumerate(parts):
         a, b = offs[k], offs[k + 1]
-        out, pp = _run_steps(U, part, params[k], 7, max_boxes=per_sim_boxes[k])
+        out, pp = _run_steps(U, part, params[k], 7, max_boxes=per_sim_boxes[k], pairs_once=pairs_once)
         assert np.array_equal(xb[a:b], out), k
         assert np.array_equal(pb[a:b] - a, pp), k
 
@@ -306,6 +309,7 @@ def test_autotuner_picks_a_valid_block(U):
     pdev = torch.stack([U.Params().as_tensor(DEV) for _ in range(6)])
     best = U.tune_batched(x, torch.from_numpy(offs.astype(np.int32)).to(DEV), pdev, 6, 2_000_000)
     assert (best.agents_per_lane, best.sweep_block) in ((1, 64), (1, 128), (2, 128))
+    assert best.pair_mode in (0, 1)
     # every configuration gives the same bits
     outs = []
     for apl, blk in ((1, 64), (1, 128), (2, 128)):
