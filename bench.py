@@ -319,8 +319,6 @@ def run_ours(args, world, rank, local, pg):
                      "traffic": sweep_traffic() if dom == "sweep" else None,
                      "avg_launch_us": avg_launch_ms * 1000.0,
                      "alg_flops_per_launch": alg_flops,
-                     "pairs_once_agent_steps_per_s": n * nsteps / (ms_once / 1e3),
-                     "pairs_once_ms_per_step": ms_once / nsteps,
                      "candidates_per_agent": cand, "contacts_per_agent": cont,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                      "note": "issue-bound: 74% of issue slots busy (ncu), see profiles/k_sweep2_lattice1m.md",
