@@ -79,7 +79,7 @@ k_sym(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
                 atomicAdd(acc + 4 * (size_t)j + 0, (unsigned long long)(-ax));
                 atomicAdd(acc + 4 * (size_t)j + 1, (unsigned long long)(-ay));
                 atomicAdd(acc + 4 * (size_t)j + 2, (unsigned long long)(-az));
-                atomicAdd(acc + 4 * (size_t)j + 3, 1ull);
+                if (!CHAINED) atomicAdd(acc + 4 * (size_t)j + 3, 1ull);   // the step needs no counts
             }
         }
         cnt = 0;
