@@ -44,7 +44,7 @@ size_t layout_workspace(void *base, uint32_t n, uint32_t nsims, uint32_t max_box
     w->counts = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (size_t)max_boxes));
     w->bounds = reinterpret_cast<uint32_t *>(
         take(sizeof(uint32_t) * kBoundsWords * (size_t)bounds_copies(nsims) * nsims));
-    w->acc = reinterpret_cast<unsigned long long *>(take(32 * (size_t)n));
+    w->acc = reinterpret_cast<unsigned long long *>(take(64 * (size_t)n));
     const size_t zero_end = off;
     w->start = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * ((size_t)max_boxes + 1)));
     w->key = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (size_t)n));

@@ -600,7 +600,9 @@ struct Workspace {
     ug_grid_info *geo;     // [nsims]
     uint32_t *bounds;      // [copies * nsims * 8]
     uint32_t *tile_sum;    // [ntiles * kTileCopies * kTileSumStride]  zero between steps
-    unsigned long long *acc;   // [n][4] fixed-point force sums of the symmetric step, zero between steps
+    unsigned long long *acc;   // [2n][4] fixed-point force sums of the every-pair-once step: the
+                               // other agents' contributions (zero between steps), then each
+                               // agent's own sums
     Ctrl *ctrl;
     uint32_t ntiles;
     size_t bytes;

@@ -122,7 +122,13 @@ k_sym(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     flush();
     if (overflow) set_status(status, UG_EBADSTATE);
     if (!valid) return;
-    if (FORWARD) {
+    if (FORWARD && CHAINED) {
+        // the step: the agent's own sums go to their own slots (no atomics),
+        // the move kernel adds the other agents' contributions
+        ulonglong2 *own = reinterpret_cast<ulonglong2 *>(acc + 4 * (size_t)n + 4 * (size_t)i);
+        own[0] = make_ulonglong2((unsigned long long)sx, (unsigned long long)sy);
+        own[1] = make_ulonglong2((unsigned long long)sz, 0ull);
+    } else if (FORWARD) {
         atomicAdd(acc + 4 * (size_t)i + 0, (unsigned long long)sx);
         atomicAdd(acc + 4 * (size_t)i + 1, (unsigned long long)sy);
         atomicAdd(acc + 4 * (size_t)i + 2, (unsigned long long)sz);
@@ -148,8 +154,9 @@ k_sym_finish(const unsigned long long *__restrict__ acc, uint32_t n, float4 *__r
                            (float)acc[4 * (size_t)i + 3]);
 }
 
-// Move kernel of the symmetric step: the fixed-point sums become F (and are
-// cleared for the next step), then the Sec. III displacement moves the agent,
+// Move kernel of the symmetric step: the other agents' contributions plus the
+// agent's own sums become F (the former cleared for the next step), then the
+// Sec. III displacement moves the agent,
 // the bounds of the moved rows accumulate, and the last CTA finalises the next
 // step's grid.
 __global__ void __launch_bounds__(256)
@@ -169,11 +176,12 @@ k_sym_move(const float4 *__restrict__ st, unsigned long long *acc, SimArgs sa, S
     if (valid) {
         const float inv = 1.0f / kFixScale;
         ulonglong2 *a2 = reinterpret_cast<ulonglong2 *>(acc + 4 * (size_t)i);
-        const ulonglong2 xy = a2[0], zc = a2[1];
+        const ulonglong2 *o2 = reinterpret_cast<const ulonglong2 *>(acc + 4 * (size_t)sa.n + 4 * (size_t)i);
+        const ulonglong2 xy = a2[0], zc = a2[1], oxy = o2[0], ozc = o2[1];
         a2[0] = make_ulonglong2(0ull, 0ull);
         a2[1] = make_ulonglong2(0ull, 0ull);
-        const float Fx = (float)(long long)xy.x * inv, Fy = (float)(long long)xy.y * inv,
-                    Fz = (float)(long long)zc.x * inv;
+        const float Fx = (float)(long long)(xy.x + oxy.x) * inv, Fy = (float)(long long)(xy.y + oxy.y) * inv,
+                    Fz = (float)(long long)(zc.x + ozc.x) * inv;
         const float4 me = __ldg(st + i);
         bool mv, cp;
         const float3 u = displacement(Fx, Fy, Fz, me.w, P, &mv, &cp);
