@@ -154,187 +154,6 @@ k_sym_finish(const unsigned long long *__restrict__ acc, uint32_t n, float4 *__r
                            (float)acc[4 * (size_t)i + 3]);
 }
 
-// ------------------------------------------------------------------ two agents per lane
-// The single-simulation form of the forward walk, with the two-agent layout of
-// the main sweep: lane l takes the box-sorted agents 2l and 2l+1, and when their
-// merged windows cannot overlap (key gap <= dims_x - 3) they share one walk per
-// sequence -- the plane above (its three runs back to back), the row above,
-// and the own run from agent 0 on -- each candidate loaded once and tested for
-// both.  Within the own run each agent takes only the candidates after it, up
-// to the end of its next box; elsewhere the extra boxes of a merged window lie
-// outside the agent's neighbourhood, so nothing is found there.  Each pair is
-// still found exactly once and its terms are the one-agent kernel's, so the
-// fixed-point sums, and the step, are the same bits.
-constexpr int kSymList = 16;   // candidates per agent between flushes
-struct __align__(16) SymLists {
-    uint32_t lst[2][kSymList][32];
-};
-
-__device__ __forceinline__ bool sym_mergeable(uint32_t k0, uint32_t k1, uint32_t dx) {
-    return k1 >= k0 && k1 - k0 + 3u <= dx;
-}
-
-struct OwnSums {
-    long long x, y, z;
-};
-
-// Exact test and Eq. 1 for the listed candidates of both agents; the pair's
-// force is added to the agent's own sums and, with the opposite sign, to the
-// candidate's fixed-point slots.  Out of line: one copy for every walk loop.
-__device__ __noinline__ void flush_sym2(const float4 *__restrict__ st, const SymLists *w, int c0,
-                                        int c1, float4 me0, float4 me1, float m2, bool exact_diffs,
-                                        ug_params P, OwnSums *own, unsigned long long *acc,
-                                        bool *overflow) {
-    const int lane = threadIdx.x & 31;
-    for (int a = 0; a < 2; ++a) {
-        const int c = a ? c1 : c0;
-        const float4 me = a ? me1 : me0;
-        const float ri = 0.5f * me.w;
-        const int m = (int)__reduce_max_sync(kFull, (unsigned)c);
-        for (int k = 0; k < m; ++k) {
-            if (k >= c) continue;
-            const uint32_t j = w->lst[a][k][lane];
-            ContactGeo g;
-            const float4 q = __ldg(st + j);
-            const bool hit = exact_diffs ? contact_t<false>(me, ri, q, m2, g)
-                                         : contact_t<true>(me, ri, q, m2, g);
-            if (!hit) continue;
-            const float coef = eq1_coef(ri, g.rb, g.rsum, g.delta, g.invd, P.k, P.gamma);
-            const float fx = __fmul_rn(coef, g.hx), fy = __fmul_rn(coef, g.hy), fz = __fmul_rn(coef, g.hz);
-            *overflow |= !(fabsf(fx) < kFixLimit && fabsf(fy) < kFixLimit && fabsf(fz) < kFixLimit);
-            const long long ax = to_fix(fx), ay = to_fix(fy), az = to_fix(fz);
-            own[a].x += ax;
-            own[a].y += ay;
-            own[a].z += az;
-            atomicAdd(acc + 4 * (size_t)j + 0, (unsigned long long)(-ax));
-            atomicAdd(acc + 4 * (size_t)j + 1, (unsigned long long)(-ay));
-            atomicAdd(acc + 4 * (size_t)j + 2, (unsigned long long)(-az));
-        }
-    }
-}
-
-__global__ void __launch_bounds__(128, 8)
-k_sym2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
-       const ug_grid_info *__restrict__ geo, SimArgs sa, unsigned long long *acc, int32_t *status,
-       const uint32_t *__restrict__ skey) {
-    __shared__ SymLists wl[4];
-    chain_begin();
-    if (cta_failed(status)) return;
-    const int lane = threadIdx.x & 31;
-    SymLists &w = wl[threadIdx.x >> 5];
-    const uint32_t n = sa.n;
-    const uint32_t i0 = (blockIdx.x * 128 + threadIdx.x) * 2u, i1 = i0 + 1u;
-    const bool v0 = i0 < n, v1 = i1 < n;
-    const ug_params P = sa.pval;
-    const ug_grid_info g = geo[0];
-    const float m2 = 2.0f * P.contact_margin;
-    const float4 far = make_float4(1e30f, 1e30f, 1e30f, 1.0f);
-    const float4 me0 = v0 ? __ldg(st + i0) : far;
-    const float4 me1 = v1 ? __ldg(st + i1) : far;
-    uint32_t k0 = 0, k1 = 0;
-    if (v0) {
-        int bx, by, bz;
-        k0 = skey ? __ldg(skey + i0) : box_key(me0, g, bx, by, bz);
-        k1 = k0;
-        if (v1) k1 = skey ? __ldg(skey + i1) : box_key(me1, g, bx, by, bz);
-    }
-    const uint32_t dx = (uint32_t)g.dims[0];
-    const int plane = g.dims[0] * g.dims[1];
-    const bool split = v1 && !sym_mergeable(k0, k1, dx);
-    const bool exact_diffs =
-        __all_sync(kFull, (!v0 || far_from_origin(me0, g.edge)) && (!v1 || far_from_origin(me1, g.edge)));
-    const FilterRow f0 = make_filter_row(me0, m2), f1 = make_filter_row(me1, m2);
-    OwnSums own[2] = {{0, 0, 0}, {0, 0, 0}};
-    bool overflow = false;
-    int c0 = 0, c1 = 0;
-    auto flush = [&]() {
-        flush_sym2(st, &w, c0, c1, me0, me1, m2, exact_diffs, P, own, acc, &overflow);
-        c0 = 0;
-        c1 = 0;
-    };
-    // sequences 0..2 (plane above, row above, own run) serve both agents, or
-    // agent 0 alone when split; 3..5 agent 1 when split
-    const int nseq = __any_sync(kFull, split) ? 6 : 3;
-#pragma unroll 1
-    for (int q = 0; q < nseq; ++q) {
-        const int kind = q < 3 ? q : q - 3;
-        bool s0 = false, s1 = false;
-        uint32_t d0 = v0 ? i0 : 0u, d1 = d0, d2 = d0;
-        int e1 = 0, e2 = 0, len = 0;
-        // accepted candidates of agent a: lo_a <= jc < lo_a + span_a
-        uint32_t lo0 = 0u, span0 = 0xffffffffu, lo1 = 0u, span1 = 0xffffffffu;
-        if (v0 && (q < 3 || split)) {
-            uint32_t lo, hi;
-            if (!split) { lo = k0; hi = k1; s0 = true; s1 = v1; }
-            else if (q < 3) { lo = k0; hi = k0; s0 = true; }
-            else { lo = k1; hi = k1; s1 = true; }
-            if (kind == 0) {              // plane above: three runs back to back
-                const uint32_t lz = lo + (uint32_t)plane, hz = hi + (uint32_t)plane;
-                const uint32_t a0 = __ldg(start + lz - dx - 1u), x0 = __ldg(start + hz - dx + 2u);
-                const uint32_t a1 = __ldg(start + lz - 1u), x1 = __ldg(start + hz + 2u);
-                const uint32_t a2 = __ldg(start + lz + dx - 1u), x2 = __ldg(start + hz + dx + 2u);
-                e1 = (int)(x0 - a0);
-                e2 = e1 + (int)(x1 - a1);
-                len = e2 + (int)(x2 - a2);
-                if (len > 0) {
-                    d0 = a0;
-                    d1 = a1 - (uint32_t)e1;
-                    d2 = a2 - (uint32_t)e2;
-                }
-            } else {
-                uint32_t b, end;
-                if (kind == 1) {          // row above
-                    b = __ldg(start + lo + dx - 1u);
-                    end = __ldg(start + hi + dx + 2u);
-                } else {                  // own run: after the agent, to the end of its next box
-                    const uint32_t own0 = i0 + 1u, end0 = __ldg(start + k0 + 2u);
-                    const uint32_t own1 = i1 + 1u, end1 = v1 ? __ldg(start + k1 + 2u) : own1;
-                    lo0 = own0;
-                    span0 = end0 - own0;
-                    lo1 = own1;
-                    span1 = end1 - own1;
-                    b = (s0 ? own0 : own1);
-                    end = (s1 ? end1 : end0);
-                }
-                len = end > b ? (int)(end - b) : 0;
-                d0 = d1 = d2 = len > 0 ? b : (v0 ? i0 : 0u);
-                e1 = e2 = len;
-            }
-        }
-        const int last = max(len - 1, 0);
-        const int lmax = (int)__reduce_max_sync(kFull, (unsigned)len);
-        for (int t = 0; t < lmax; t += kSweepUnroll) {
-#pragma unroll
-            for (int u = 0; u < kSweepUnroll; ++u) {
-                const int tt = min(t + u, last);
-                const uint32_t jc = (uint32_t)tt + (tt < e1 ? d0 : (tt < e2 ? d1 : d2));
-                const float4 qrow = __ldg(st + jc);
-                const bool in = t + u < len;
-                if (in & s0 & (jc - lo0 < span0) & (jc != i0) & prefilter(qrow, f0)) {
-                    w.lst[0][c0][lane] = jc;
-                    ++c0;
-                }
-                if (in & s1 & (jc - lo1 < span1) & (jc != i1) & prefilter(qrow, f1)) {
-                    w.lst[1][c1][lane] = jc;
-                    ++c1;
-                }
-            }
-            if (__any_sync(kFull, max(c0, c1) > kSymList - kSweepUnroll)) flush();
-        }
-    }
-    flush();
-    if (overflow) set_status(status, UG_EBADSTATE);
-    ulonglong2 *own_slots = reinterpret_cast<ulonglong2 *>(acc + 4 * (size_t)n);
-    if (v0) {
-        own_slots[2 * (size_t)i0] = make_ulonglong2((unsigned long long)own[0].x, (unsigned long long)own[0].y);
-        own_slots[2 * (size_t)i0 + 1] = make_ulonglong2((unsigned long long)own[0].z, 0ull);
-    }
-    if (v1) {
-        own_slots[2 * (size_t)i1] = make_ulonglong2((unsigned long long)own[1].x, (unsigned long long)own[1].y);
-        own_slots[2 * (size_t)i1 + 1] = make_ulonglong2((unsigned long long)own[1].z, 0ull);
-    }
-}
-
 // Move kernel of the symmetric step: the other agents' contributions plus the
 // agent's own sums become F (the former cleared for the next step), then the
 // Sec. III displacement moves the agent,
@@ -381,12 +200,8 @@ void launch_sym_step(const float4 *sorted, const uint32_t *start, const ug_grid_
                      const SimArgs &sa, const SweepOut &out, unsigned long long *acc,
                      int32_t *status, cudaStream_t s, const uint32_t *skey) {
     const uint32_t n = sa.n;
-    if (sa.nsims == 1 && sa.offset == nullptr)
-        launch_chained(k_sym2, (unsigned)((n + 255) / 256), 128u, s, sorted, start, geo, sa, acc, status,
-                       skey);
-    else
-        launch_chained(k_sym<true, true>, (unsigned)((n + 127) / 128), 128u, s, sorted, start, geo, sa,
-                       acc, status, skey);
+    launch_chained(k_sym<true, true>, (unsigned)((n + 127) / 128), 128u, s, sorted, start, geo, sa,
+                   acc, status, skey);
     launch_chained(k_sym_move, (unsigned)((n + 255) / 256), 256u, s, sorted, acc, sa, out, status);
 }
 
