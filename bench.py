@@ -45,8 +45,8 @@ FLOPS_PER_AGENT = 25
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one k_sweep2 launch on this workload, from the
 # ncu capture summarised in profiles/k_sweep2_lattice1m.md (cache flushed)
-SWEEP_DRAM_BYTES = 23.515904e6 + 0.515328e6
-SWEEP_DRAM_BYTES_SRC = "4fd8c07749c415c0"      # sha256[:16] of ug_sweep2.cu + ug_internal.cuh when captured
+SWEEP_DRAM_BYTES = 23.516928e6 + 0.438272e6
+SWEEP_DRAM_BYTES_SRC = "cae48946f722d800"      # sha256[:16] of ug_sweep2.cu + ug_internal.cuh when captured
 
 
 def sweep_traffic():
