@@ -63,3 +63,30 @@ def test_workspace_too_small_is_rejected_on_the_host(U):
     rc = lib.ug_step(U._ptr(x), U._ptr(perm), len(st), U.Params().c(), 1, 10000, U._ptr(ws),
                      ws.numel(), U._ptr(status), U._stream())
     assert rc == U.UG_EWORKSPACE and int(status.item()) == 0
+
+
+def test_pairs_once_error_stops_the_rest_of_the_call(U):
+    st = P.small_uniform(2)
+    st[7, 1] = np.inf
+    x = torch.from_numpy(st).to(DEV)
+    sp = U.Stepper(len(st), 100000, x.device)
+    perm = U.iota(len(st), x.device)
+    before = x.clone()
+    sp.step(x, perm, U.Params(), 5, pairs_once=True)
+    with pytest.raises(U.UgError) as e:
+        sp.check()
+    assert e.value.code == U.UG_EBADSTATE
+    assert torch.equal(x, before)                         # rows untouched
+    _healthy(U)
+
+
+def test_fixed_point_overflow_is_reported(U):
+    """A force component beyond the fixed-point range (2^30) is recorded as
+    UG_EBADSTATE instead of wrapping around silently."""
+    st = P.small_uniform(5)
+    x = torch.from_numpy(st).to(DEV)
+    srt, perm, start, info, _ = U.grid_build(x)
+    with pytest.raises(U.UgError) as e:
+        U.forces_symmetric(srt, start, info, U.Params(k=1e12))
+    assert e.value.code == U.UG_EBADSTATE
+    _healthy(U)
