@@ -450,16 +450,24 @@ class Simulation:
         self.by_id = torch.empty_like(self.x)
 
     def run(self, state_host: torch.Tensor, params: Params, nsteps: int,
-            out_host: torch.Tensor | None = None) -> torch.Tensor:
+            out_host: torch.Tensor | None = None, pairs_once: bool = False,
+            sync: bool = True) -> torch.Tensor:
+        """Rows in id order in, nsteps steps, rows in id order out.  With sync
+        (the default) the call waits for the copy back and raises on a device
+        error; with sync=False the caller synchronises the current stream and
+        calls stepper.check() before reading out_host."""
         if out_host is None:
             out_host = torch.empty((self.n, 4), dtype=torch.float32, pin_memory=True)
         self.x.copy_(state_host, non_blocking=True)
         lib = self.stepper.lib
         _check(lib.ug_iota(_ptr(self.perm), self.n, _stream()), "ug_iota")
-        self.stepper.step(self.x, self.perm, params, nsteps)
+        self.stepper.step(self.x, self.perm, params, nsteps, pairs_once=pairs_once)
         _check(lib.ug_scatter_rows(_ptr(self.x), _ptr(self.perm), self.n, _ptr(self.by_id),
                                    _stream()), "ug_scatter_rows")
         out_host.copy_(self.by_id, non_blocking=True)
+        if sync:
+            torch.cuda.current_stream(self.device).synchronize()
+            self.stepper.check("Simulation.run")
         return out_host
 
 

@@ -530,3 +530,19 @@ def test_pairs_once_step_against_oracle(U, name):
     b, pb = _run_steps(U, st, U.Params(adherence=0.0), 3)
     ga, gb = by_id(a.astype(np.float64), pa), by_id(b.astype(np.float64), pb)
     assert np.abs(ga[:, :3] - gb[:, :3]).max() < 1e-3
+
+
+@pytest.mark.parametrize("pairs_once", [False, True])
+def test_simulation_run_host_to_host(U, pairs_once):
+    """The end-to-end API: host rows in id order in, host rows in id order out,
+    the same bits as the device-side steps."""
+    st = P.small_uniform(6)
+    n = len(st)
+    mb = U.estimate_max_boxes(_gpu(st), 0.0, slack=2.0)
+    sim = U.Simulation(n, mb, DEV)
+    host_in = torch.from_numpy(st).pin_memory()
+    out = sim.run(host_in, U.Params(), 4, pairs_once=pairs_once).numpy().copy()
+    dev, perm = _run_steps(U, st, U.Params(), 4, max_boxes=mb, pairs_once=pairs_once)
+    assert np.array_equal(out, by_id(dev, perm))
+    again = sim.run(host_in, U.Params(), 4, pairs_once=pairs_once).numpy()
+    assert np.array_equal(out, again)                 # buffers reused, same result
