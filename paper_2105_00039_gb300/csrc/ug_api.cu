@@ -27,9 +27,8 @@ int device_sm_count() {
 
 static uint32_t bounds_copies(uint32_t nsims) { return nsims == 1 ? kBoundsCopiesSingle : 1u; }
 
-// Layout (base may be null to size only).  The first five regions (ctrl, tile
-// sums, counts, bounds, fixed-point force sums) are contiguous and are the only
-// ones that need zeroing.
+// Layout (base may be null to size only).  The first four regions (ctrl, tile
+// sums, counts, bounds) are contiguous and are the only ones every call zeroes.
 size_t layout_workspace(void *base, uint32_t n, uint32_t nsims, uint32_t max_boxes, Workspace *w) {
     size_t off = 0;
     char *b = static_cast<char *>(base);
@@ -44,7 +43,6 @@ size_t layout_workspace(void *base, uint32_t n, uint32_t nsims, uint32_t max_box
     w->counts = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (size_t)max_boxes));
     w->bounds = reinterpret_cast<uint32_t *>(
         take(sizeof(uint32_t) * kBoundsWords * (size_t)bounds_copies(nsims) * nsims));
-    w->acc = reinterpret_cast<unsigned long long *>(take(64 * (size_t)n));
     const size_t zero_end = off;
     w->start = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * ((size_t)max_boxes + 1)));
     w->key = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (size_t)n));
@@ -53,6 +51,8 @@ size_t layout_workspace(void *base, uint32_t n, uint32_t nsims, uint32_t max_box
     w->sorted = reinterpret_cast<float4 *>(take(sizeof(float4) * (size_t)n));
     w->perm2 = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (size_t)n));
     w->geo = reinterpret_cast<ug_grid_info *>(take(sizeof(ug_grid_info) * (size_t)nsims));
+    // fixed-point sums of the every-pair-once step (zeroed by run_steps when used)
+    w->acc = reinterpret_cast<unsigned long long *>(take(64 * (size_t)n));
     w->bytes = off;
     (void)zero_end;
     return off;
@@ -73,6 +73,10 @@ int run_steps(float4 *state, uint32_t *perm, const SimArgs &sa, int nsteps, uint
         if (events) cudaEventRecord(events[k], s);
     };
     if (cudaMemsetAsync(w.ctrl, 0, zero_bytes(w), s) != cudaSuccess) return UG_ECUDA;
+    // the every-pair-once step adds the other agents' contributions into the
+    // first half of w.acc; its move kernel leaves that half zero after each step
+    if (agents_per_lane == 3 && cudaMemsetAsync(w.acc, 0, 32 * (size_t)n, s) != cudaSuccess)
+        return UG_ECUDA;
     mark(0);
     launch_bounds(state, sa, w, w.geo, max_boxes, status, s);
     uint32_t *pcur = perm, *pnext = w.perm2;
