@@ -357,7 +357,9 @@ def run_ours(args, world, rank, local, pg):
                        "unit": "agent-steps/s", "h2d_bytes_per_step": 16 * n,
                        "d2h_bytes_per_step": 16 * n}
 
-    if not args.no_extras:
+    # the extra rows are single-GPU measurements: rank 0 takes them alone (the
+    # other ranks of a multi-GPU run only contribute to the headline)
+    if not args.no_extras and rank == 0:
         line["batched"] = measure_batched(dev, flush)
         line["adjoint"] = measure_adjoint(dev, flush)
         line["density_sweep"] = measure_density(dev, flush)
