@@ -357,9 +357,9 @@ def run_ours(args, world, rank, local, pg):
                        "unit": "agent-steps/s", "h2d_bytes_per_step": 16 * n,
                        "d2h_bytes_per_step": 16 * n}
 
-    # the extra rows are single-GPU measurements: rank 0 takes them alone (the
-    # other ranks of a multi-GPU run only contribute to the headline)
-    if not args.no_extras and rank == 0:
+    # the extra rows and the CPU baselines are single-GPU measurements: a
+    # multi-GPU run reports only the headline
+    if not args.no_extras and world == 1:
         line["batched"] = measure_batched(dev, flush)
         line["adjoint"] = measure_adjoint(dev, flush)
         line["density_sweep"] = measure_density(dev, flush)
@@ -367,7 +367,7 @@ def run_ours(args, world, rank, local, pg):
         line["lattice_margin"] = measure_lattice_margin(dev, flush)
         line["pairs_once"] = measure_pairs_once(dev, flush)
 
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, secs = cpu_oracle_rate(st, 3)
         line["cpu_baseline"] = {"value": rate, "unit": "agent-steps/s", "cores": 1, "kind": "oracle",
                                 "sample": f"3 FP64 oracle steps of all 2^20 cells ({secs:.1f} s)"}
