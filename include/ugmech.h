@@ -20,13 +20,14 @@
  *     256-byte aligned.  Its contents need not be initialised and are
  *     clobbered.
  *   - Agent state is float32, 4 floats per agent: (x, y, z, diameter), 16-byte
- *     aligned.  At most 2^30 agents per call (UG_EINVAL above).  Forces and gradients use the same 4-float rows.
+ *     aligned.  Forces and gradients use the same 4-float rows.  At most 2^30
+ *     agents per call (UG_EINVAL above).
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call is
  *     asynchronous: the return value reports argument and launch errors only.
  *     Errors found on the device (bad input values, grid too large, a list
- *     overflow) are written to `*status` (a device int32
- *     the caller zeroes before the first call; the first error wins and later
- *     kernels of the same call become no-ops).  Read it after synchronising.
+ *     overflow) are written to `*status`, a device int32 the caller zeroes
+ *     before the first call; the first error wins and later kernels of the
+ *     same call become no-ops.  Read it after synchronising.
  *   - Calls on different streams must use different workspaces.  The library
  *     keeps no state between calls and is safe to call from several host
  *     threads with distinct workspaces.
@@ -119,9 +120,9 @@ typedef struct {
 
 /* ------------------------------------------------------------------ workspace */
 
-/* Bytes of workspace needed by ug_grid_build / ug_step / ug_step_batched for
- * n agents in nsims simulations with room for max_boxes grid boxes (summed over
- * the simulations). */
+/* Bytes of workspace needed by ug_grid_build, ug_step, ug_step_pairs_once,
+ * ug_step_traced and ug_step_batched for n agents in nsims simulations with
+ * room for max_boxes grid boxes (summed over the simulations). */
 size_t ug_workspace_bytes(uint32_t n, uint32_t nsims, uint32_t max_boxes);
 
 /* ------------------------------------------------------------------ grid build */
