@@ -23,16 +23,23 @@ constexpr float kFixLimit = 1073741824.0f;            // |force component| < 2^3
 
 __device__ __forceinline__ long long to_fix(float v) { return __float2ll_rn(v * kFixScale); }
 
+// Candidates listed per agent between flushes: longer than the main sweep's
+// lists, since a flush here costs three atomics per pair.
+constexpr int kSymCap = 28;
+struct SymList {
+    uint32_t lst[kSymCap][32];
+};
+
 template <bool FORWARD, bool CHAINED>
 __global__ void __launch_bounds__(128)
 k_sym(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
       const ug_grid_info *__restrict__ geo, SimArgs sa,
       unsigned long long *acc, int32_t *status, const uint32_t *__restrict__ skey) {
-    __shared__ WarpLists wl[4];
+    __shared__ SymList wl[4];
     if (CHAINED) chain_begin();
     if (cta_failed(status)) return;
     const int lane = threadIdx.x & 31;
-    WarpLists &w = wl[threadIdx.x >> 5];
+    SymList &w = wl[threadIdx.x >> 5];
     const uint32_t n = sa.n;
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < n;
@@ -116,7 +123,7 @@ k_sym(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
                     ++cnt;
                 }
             }
-            if (__any_sync(kFull, cnt > kListCap - kSweepUnroll)) flush();
+            if (__any_sync(kFull, cnt > kSymCap - kSweepUnroll)) flush();
         }
     }
     flush();
