@@ -310,8 +310,10 @@ int ug_forces_ladder(int32_t version, const float *state, uint32_t n, ug_params 
  * accumulated as 64-bit fixed point (units of 2^-32) with integer atomics, so
  * both modes are deterministic and give the same bits; the float-float contact
  * test and Eq. 1 are the main path's, summed in fixed point rather than with
- * compensated float32 sums.  A force component of 2^30 or more records
- * UG_EBADSTATE.
+ * compensated float32 sums.  A pair force component of 2^30 or more records
+ * UG_EBADSTATE; a per-agent sum holds |F| < 2^31 force units (with the
+ * default constants and diameters ~10, Eq. 1's pair forces are a few tens of
+ * units, far inside this range).
  *   ws  >= 32 * n bytes, 256-B aligned (the fixed-point accumulators) */
 int ug_forces_symmetric(int32_t each_pair_once, const float *state_sorted, const uint32_t *box_start,
                         const ug_grid_info *info, uint32_t n, ug_params p, float *force, void *ws,

@@ -18,8 +18,13 @@
 
 namespace ug {
 
+// Fixed point: 2^-32 force units in int64, so a sum holds |F| < 2^31 units.
+// Each pair's components are checked against 2^30 (reported as UG_EBADSTATE);
+// with the default constants and diameters ~10 a pair force (kappa delta -
+// gamma sqrt(R delta)) is a few tens of units, so a sum stays far inside the
+// range for any realistic number of overlapping neighbours.
 constexpr float kFixScale = 4294967296.0f;           // 2^32
-constexpr float kFixLimit = 1073741824.0f;            // |force component| < 2^30
+constexpr float kFixLimit = 1073741824.0f;            // |force component| < 2^30 per pair
 
 __device__ __forceinline__ long long to_fix(float v) { return __float2ll_rn(v * kFixScale); }
 
@@ -163,9 +168,8 @@ k_sym_finish(const unsigned long long *__restrict__ acc, uint32_t n, float4 *__r
 
 // Move kernel of the symmetric step: the other agents' contributions plus the
 // agent's own sums become F (the former cleared for the next step), then the
-// Sec. III displacement moves the agent,
-// the bounds of the moved rows accumulate, and the last CTA finalises the next
-// step's grid.
+// Sec. III displacement moves the agent, the bounds of the moved rows
+// accumulate, and the last CTA finalises the next step's grid.
 __global__ void __launch_bounds__(256)
 k_sym_move(const float4 *__restrict__ st, unsigned long long *acc, SimArgs sa, SweepOut out,
            int32_t *status) {
