@@ -6,13 +6,20 @@
     in delta is Eq. 1's magnitude (an independent route to the same numbers);
   * Newton's third law, rotation/permutation/scaling invariance;
   * brute-force pair search as the definition of the kd-tree search;
-  * the uniform grid's completeness condition (Sec. IV-A): every contact pair
-    lies in adjacent boxes;
+  * closed-form displacements (Sec. III rules as read here: strict adherence,
+    u = (dt / m) F with m = density (pi/6) d^3, the cap along u), with dt != 1
+    and a capped case;
+  * a hand-worked grid (edge, padding layer, x-fastest keys, exclusive starts)
+    and the uniform grid's completeness condition (Sec. IV-A): every contact
+    pair lies in adjacent boxes;
   * the adjoint against FP64 central finite differences of the forward.
 
 Plausible mistakes planted in the oracle (on the CPU) must trip at least one pin
-(test_planted_mistakes_are_caught).
+(test_planted_mistakes_are_caught): in Eq. 1 (a dropped term, a sign, an index,
+the radius), in the displacement (threshold, mass, dt, cap) and in the grid
+(padding, key order, scan).
 """
+import dataclasses
 import json
 import math
 import os
@@ -119,6 +126,49 @@ def check_grid_completeness(state32, margin=0.0):
     return ok
 
 
+def check_displacement_hand():
+    """Worst relative deviation from hand-derived displacements (Sec. III rules
+    as read here: strict adherence threshold, u = (dt / m) F with
+    m = density (pi/6) d^3, cap to max_disp along u).  The parameters are
+    float32-rounded by the oracle, hence the 1e-7 allowance."""
+    worst = 0.0
+
+    def rel(a, b):
+        a, b = np.asarray(a, float), np.asarray(b, float)
+        return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+    # |F| = kappa delta = 0.5 exactly, threshold 0.5: no motion (strict >)
+    r = O.step(np.array([[0, 0, 0, 10], [9.5, 0, 0, 10]], float),
+               O.Params(k=1.0, gamma=0.0, adherence=0.5), method="brute")
+    worst = max(worst, float(np.abs(r["u"]).max()))
+    # deep overlap (phi = 10 - sqrt(12.5)), dt = 1/2, d = 10: m = 0.02 pi/6 1000
+    deep = np.array([[0, 0, 0, 10], [0, 5, 0, 10]], float)
+    u_half = 0.5 * (10.0 - math.sqrt(12.5)) / (0.02 * math.pi / 6.0 * 1000.0)   # 0.30866
+    r = O.step(deep, O.Params(dt=0.5), method="brute")
+    worst = max(worst, rel(r["u"], [[0, -u_half, 0], [0, u_half, 0]]))
+    # the same with max_disp 0.2 < 0.30866: |u| = 0.2 along the same line
+    r = O.step(deep, O.Params(dt=0.5, max_disp=0.2), method="brute")
+    worst = max(worst, rel(r["u"], [[0, -0.2, 0], [0, 0.2, 0]]))
+    # a d = 20 sphere against a d = 10 one with delta = 1 and gamma = 0: |F| = 1,
+    # m = 0.02 pi/6 8000, so |u| = 1/(0.02 pi/6 8000) for the large one
+    r = O.step(np.array([[0, 0, 0, 20], [14, 0, 0, 10]], float),
+               O.Params(k=1.0, gamma=0.0, adherence=0.0), method="brute")
+    worst = max(worst, rel(r["u"][0], [-1.0 / (0.02 * math.pi / 6.0 * 8000.0), 0, 0]))
+    return 0.0 if worst < 1e-7 else worst
+
+
+def check_grid_hand():
+    """Two d = 10 spheres at x = 0 and x = 25: edge 10 + 8 ulp(25) = 10 + 2^-16,
+    one empty padding layer, so boxes (1,1,1) and (3,1,1) of a 5x3x3 grid,
+    x-fastest keys 21 and 23, starts 0 | 1 | 2 around them."""
+    g = O.grid(np.array([[0, 0, 0, 10], [25, 0, 0, 10]], dtype=np.float32))
+    e = np.float32(10.0 + 2.0 ** -16)
+    return bool(g["edge"] == e and np.array_equal(g["origin"], [-e, -e, -e])
+                and list(g["dims"]) == [5, 3, 3] and list(g["key"]) == [21, 23]
+                and g["nboxes"] == 45 and list(g["perm"]) == [0, 1]
+                and list(g["start"][20:25]) == [0, 0, 1, 1, 2] and g["start"][-1] == 2)
+
+
 # ------------------------------------------------------------------ tests
 def test_worked_examples():
     assert check_worked_examples() < 1e-12
@@ -204,14 +254,12 @@ def test_pair_count_small_lattice():
 
 
 def test_grid_hand_example():
-    st = np.array([[0, 0, 0, 10], [25, 0, 0, 10]], dtype=np.float32)
-    g = O.grid(st)
     # S = 10, C = 25: ulp(25) = 2^-19, edge = 10 + 8 * 2^-19 = 10 + 2^-16
-    e = 10.0 + 2.0 ** -16
-    assert g["edge"] == np.float32(e) and np.array_equal(g["origin"], np.float32([-e, -e, -e]))
-    assert list(g["dims"]) == [5, 3, 3]
-    assert list(g["key"]) == [21, 23] and g["nboxes"] == 45
-    assert g["start"][21] == 0 and g["start"][22] == 1 and g["start"][24] == 2
+    assert check_grid_hand()
+
+
+def test_displacement_hand_values():
+    assert check_displacement_hand() == 0.0
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
@@ -379,22 +427,54 @@ def _plant(monkeypatch, which):
             r["u"] = np.where(mv[:, None], r["v"], 0.0)
             return r
         monkeypatch.setattr(M, "displacement", disp)
+    elif which == "mass_from_radius":
+        monkeypatch.setattr(M, "mass", lambda diam, prm: prm.density * (np.pi / 6.0) * (0.5 * diam) ** 3)
+    elif which == "dt_ignored":
+        monkeypatch.setattr(M, "displacement",
+                            lambda F, diam, prm: orig_disp(F, diam, dataclasses.replace(prm, dt=1.0)))
+    elif which == "cap_ignored":
+        monkeypatch.setattr(M, "displacement",
+                            lambda F, diam, prm: orig_disp(F, diam, dataclasses.replace(prm, max_disp=np.inf)))
+    elif which.startswith("grid_"):
+        orig_grid = M.grid
+
+        def grid(state32, contact_margin=0.0):
+            g = dict(orig_grid(state32, contact_margin))
+            b, dims = g["box"].copy(), g["dims"].copy()
+            if which == "grid_no_padding":          # origin at the minimum, no empty layer
+                b, dims = b - 1, dims - 1
+            if which == "grid_key_y_fastest":
+                key = (b[:, 2] * dims[0] + b[:, 0]) * dims[1] + b[:, 1]
+            else:
+                key = (b[:, 2] * dims[1] + b[:, 1]) * dims[0] + b[:, 0]
+            nboxes = int(np.prod(dims))
+            counts = np.bincount(key, minlength=nboxes)
+            start = np.zeros(nboxes + 1, dtype=np.int64)
+            if which == "grid_inclusive_scan":
+                start[:-1] = np.cumsum(counts)
+                start[-1] = start[-2]
+            else:
+                start[1:] = np.cumsum(counts)
+            g.update(box=b, dims=dims, key=key, nboxes=nboxes, counts=counts, start=start,
+                     perm=np.argsort(key, kind="stable"))
+            return g
+        monkeypatch.setattr(M, "grid", grid)
+        monkeypatch.setattr(O, "grid", grid)
 
 
 def _pins_pass(which):
     g_ok = check_worked_examples() < 1e-12
     p_ok = check_potential_gradient(n=16, seed=3) < 1e-7
     n_ok = check_newton3(P.small_uniform(0)[:1500]) < 1e-13
-    d_ok = True
-    if which == "adherence_ge":
-        prm = O.Params(k=1.0, gamma=0.0, adherence=0.5)
-        r = M.step(np.array([[0, 0, 0, 10], [9.5, 0, 0, 10]], float), prm, method="brute")
-        d_ok = not r["moving"].any()
-    return g_ok and p_ok and n_ok and d_ok
+    d_ok = check_displacement_hand() == 0.0
+    b_ok = check_grid_hand() and check_grid_completeness(P.small_uniform(0))
+    return g_ok and p_ok and n_ok and d_ok and b_ok
 
 
 @pytest.mark.parametrize("which", ["drop_gamma", "wrong_sign", "diameter_as_radius", "R_sum",
-                                   "transposed_index", "adherence_ge"])
+                                   "transposed_index", "adherence_ge", "mass_from_radius",
+                                   "dt_ignored", "cap_ignored", "grid_no_padding",
+                                   "grid_key_y_fastest", "grid_inclusive_scan"])
 def test_planted_mistakes_are_caught(monkeypatch, which):
     assert _pins_pass("none")
     _plant(monkeypatch, which)
