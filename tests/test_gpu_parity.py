@@ -419,28 +419,34 @@ def test_simulate_host_round_trip(U):
 
 
 # ------------------------------------------------------------------ full-size, sampled
-def _sampled_check(U, x, prm_o, prm_u, nsample=3000, seed=0):
+def _sampled_check(U, x, prm_o, prm_u, nsample=3000, seed=0, symmetric=False):
     """Grid + forces of the GPU's own current rows, compared agent by agent
-    with the oracle on a random sample of agents."""
+    with the oracle on a random sample of agents; with symmetric=True the
+    every-pair-once forces (ug_forces_symmetric) of the same grid as well."""
     srt, perm, start, info, _ = U.grid_build(x, contact_margin=prm_u.contact_margin,
                                              max_boxes=U.estimate_max_boxes(x, prm_u.contact_margin))
-    F = U.compute_forces(srt, start, info, prm_u)
+    forces = [U.compute_forces(srt, start, info, prm_u)]
+    if symmetric:
+        forces.append(U.forces_symmetric(srt, start, info, prm_u))
     st = x.cpu().numpy()
-    Fg = by_id(F.cpu().numpy().astype(np.float64), perm.cpu().numpy())
+    pid = perm.cpu().numpy()
     idx = np.random.default_rng(seed).choice(len(st), size=min(nsample, len(st)), replace=False)
     ref = O.step_sampled(st, idx, prm_o)
-    per, norm, bad = force_errors(Fg[idx, :3], ref["F"], ref["S"])
-    assert per <= TOL_STEP and bad == 0, (per, bad)
-    assert np.array_equal(Fg[idx, 3].astype(np.int64), ref["npairs"])
-    tot = Fg[:, :3].sum(0)
-    assert np.abs(tot).max() <= 1e-4 * np.abs(Fg[:, :3]).sum(0).max()   # Newton's third law
+    for F in forces:
+        Fg = by_id(F.cpu().numpy().astype(np.float64), pid)
+        per, norm, bad = force_errors(Fg[idx, :3], ref["F"], ref["S"])
+        assert per <= TOL_STEP and bad == 0, (per, bad)
+        assert np.array_equal(Fg[idx, 3].astype(np.int64), ref["npairs"])
+        tot = Fg[:, :3].sum(0)
+        assert np.abs(tot).max() <= 1e-4 * np.abs(Fg[:, :3]).sum(0).max()   # Newton's third law
     return float(ref["npairs"].mean())
 
 
-def test_full_size_lattice_1m_100_steps(U):
-    """The benchmark's configuration: 2^20 lattice cells, 100 fused steps; the
-    rows the GPU holds before the first and after the last step are checked
-    agent by agent."""
+@pytest.mark.parametrize("pairs_once", [False, True])
+def test_full_size_lattice_1m_100_steps(U, pairs_once):
+    """The benchmark's configuration: 2^20 lattice cells, 100 fused steps (the
+    gather step or every pair once); the rows the GPU holds before the first
+    and after the last step are checked agent by agent."""
     st = P.lattice_1m(0)
     x = _gpu(st)
     n = len(st)
@@ -449,19 +455,78 @@ def test_full_size_lattice_1m_100_steps(U):
     assert 3.0 < nb0 < 7.0
     sp = U.Stepper(n, mb, x.device)
     perm = U.iota(n, x.device)
-    sp.step(x, perm, U.Params(), 100)
+    sp.step(x, perm, U.Params(), 100, pairs_once=pairs_once)
     sp.check()
     p = perm.cpu().numpy()
     assert np.array_equal(np.sort(p), np.arange(n))
     _sampled_check(U, x, O.Params(), U.Params(), seed=1)
 
 
-@pytest.mark.parametrize("nbar", [2, 8, 32, 64])
-def test_density_sweep_4m_sampled(U, nbar):
-    st = P.density_cube(1 << 22, float(nbar), seed=nbar)
+@pytest.mark.parametrize("n,nbar", [(1 << 22, 2), (1 << 22, 8), (1 << 22, 32), (1 << 22, 64),
+                                    (1 << 24, 12)])
+def test_density_sweep_sampled(U, n, nbar):
+    """The density sweep's populations at full size (4M cells at 2 to 64 mean
+    neighbours, 16M at 12, the seeds the benchmark uses): gather and
+    every-pair-once forces against the oracle on a sample of agents."""
+    st = P.density_cube(n, float(nbar), seed=nbar)
     x = _gpu(st)
-    nb = _sampled_check(U, x, O.Params(max_disp=0.0), U.Params(max_disp=0.0), nsample=1500)
+    nb = _sampled_check(U, x, O.Params(max_disp=0.0), U.Params(max_disp=0.0), nsample=1500,
+                        symmetric=True)
     assert 0.6 * nbar < nb < 1.2 * nbar
+
+
+@pytest.mark.parametrize("pairs_once", [False, True])
+def test_batched_full_population(U, pairs_once):
+    """The batched workload at full size: 256 simulations (log-uniform counts in
+    [1e3, 2e5], mean neighbours U[4, 40]).  One batched step against the oracle
+    on a sample of agents of four simulations, then 50 batched steps bit for bit
+    against each simulation run alone with the plain step of the same method."""
+    nsims = 256
+    st, offs = P.batched_population(nsims=nsims, seed=0)
+    n = len(st)
+    x0 = _gpu(st)
+    offs_t = torch.from_numpy(offs.astype(np.int32)).to(DEV)
+    prm = U.Params()
+    pdev = torch.stack([prm.as_tensor(DEV) for _ in range(nsims)])
+    caps = [4 * U.estimate_max_boxes(x0[int(offs[k]):int(offs[k + 1])], 0.0, slack=1.0,
+                                     extra_extent=24.0) + 1000 for k in range(nsims)]
+    sp = U.Stepper(n, int(sum(caps)), x0.device, nsims=nsims)
+    t = U.ug_tuning()
+    t.pair_mode = 1 if pairs_once else 0
+    # one step against the oracle
+    x = x0.clone()
+    perm = U.iota(n, x.device)
+    sp.step_batched(x, perm, offs_t, pdev, 1, t)
+    sp.check("batched-1")
+    new = by_id(x.cpu().numpy().astype(np.float64), perm.cpu().numpy())
+    rng = np.random.default_rng(1)
+    for k in (0, 85, 170, 255):
+        a, b = int(offs[k]), int(offs[k + 1])
+        part = st[a:b]
+        idx = rng.choice(b - a, size=min(300, b - a), replace=False)
+        ref = O.step_sampled(part, idx, O.Params())
+        flips = adherence_flips(ref["Fn"], ref["S"], 0.1)
+        scale = ref["S"] / O.mass(part[idx, 3].astype(np.float64), O.Params().as64())
+        got = new[a:b][idx, :3]
+        want = part[idx, :3].astype(np.float64) + ref["u"]
+        ok = np.abs(got - want) <= ulp32(got) + TOL_STEP * np.maximum(
+            np.linalg.norm(ref["u"], axis=1), scale)[:, None]
+        assert ok[~flips].all(), (k, np.argwhere(~ok)[:5])
+    # 50 steps, batched vs alone
+    x = x0.clone()
+    perm = U.iota(n, x.device)
+    sp.step_batched(x, perm, offs_t, pdev, 50, t)
+    sp.check("batched-50")
+    xb, pb = x.cpu().numpy(), perm.cpu().numpy()
+    for k in range(nsims):
+        a, b = int(offs[k]), int(offs[k + 1])
+        y = x0[a:b].clone()
+        py = U.iota(b - a, y.device)
+        alone = U.Stepper(b - a, caps[k], y.device)
+        alone.step(y, py, prm, 50, pairs_once=pairs_once)
+        alone.check("alone")
+        assert np.array_equal(xb[a:b], y.cpu().numpy()), k
+        assert np.array_equal(pb[a:b] - a, py.cpu().numpy()), k
 
 
 def _thin_slab(n, thickness, side, seed):
