@@ -110,7 +110,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -368,10 +368,10 @@ def run_ours(args, world, rank, local, pg):
         line["pairs_once"] = measure_pairs_once(dev, flush)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, secs = cpu_oracle_rate(st, 3)
+        rate, secs = cpu_oracle_rate(st, 6)
         line["cpu_baseline"] = {"value": rate, "unit": "agent-steps/s", "cores": 1, "kind": "oracle",
-                                "sample": f"3 FP64 oracle steps of all 2^20 cells ({secs:.1f} s)"}
-        line["cpu_grid_baseline"] = cpu_grid_rate(st, 3)
+                                "sample": f"6 FP64 oracle steps of all 2^20 cells ({secs:.1f} s)"}
+        line["cpu_grid_baseline"] = cpu_grid_rate(st, 50)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
