@@ -45,8 +45,8 @@ FLOPS_PER_AGENT = 25
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one k_sweep2 launch on this workload, from the
 # ncu capture summarised in profiles/k_sweep2_lattice1m.md (cache flushed)
-SWEEP_DRAM_BYTES = 23.516928e6 + 0.438272e6
-SWEEP_DRAM_BYTES_SRC = "cae48946f722d800"      # sha256[:16] of ug_sweep2.cu + ug_internal.cuh when captured
+SWEEP_DRAM_BYTES = 23.521792e6 + 0.320256e6
+SWEEP_DRAM_BYTES_SRC = "9b362eb61c0f7119"      # sha256[:16] of ug_sweep2.cu + ug_internal.cuh when captured
 
 
 def sweep_traffic():
@@ -321,7 +321,7 @@ def run_ours(args, world, rank, local, pg):
                      "alg_flops_per_launch": alg_flops,
                      "candidates_per_agent": cand, "contacts_per_agent": cont,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                     "note": "issue-bound: 74% of issue slots busy (ncu), see profiles/k_sweep2_lattice1m.md",
+                     "note": "instruction issue: 68% of issue slots busy, 89.7M warp instructions per launch (ncu), see profiles/k_sweep2_lattice1m.md",
                      "hbm": {"achieved_gbs": achieved, "peak_gbs": hbm, "frac": achieved / hbm,
                              "alg_bytes_per_launch": alg_bytes,
                              "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},

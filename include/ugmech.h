@@ -210,7 +210,7 @@ int ug_step(float *state, uint32_t *perm, uint32_t n, ug_params p, int32_t nstep
  * atomics, so still deterministic), after which a second kernel moves the
  * agents.  Same arguments, workspace and results within the same tolerance as
  * ug_step, but not the same bits (fixed-point instead of compensated float32
- * sums).  It pays in dense grids: 1.75x at ~32 and 1.9x at ~64 neighbours per
+ * sums).  It pays in dense grids: 1.7x at ~32 and 1.9x at ~64 neighbours per
  * agent on GB300, while on sparse grids (a few agents per box) the atomics cost
  * more than the halved walk saves and ug_step is faster.  For many simulations
  * use ug_step_batched with tuning->pair_mode = 1. */

@@ -275,35 +275,35 @@ __device__ __forceinline__ bool far_from_origin(const float4 &a, float e) {
 // consecutive boxes, one per (dy, dz): run (dy, dz) covers sorted slots
 // start[k + dz*plane + dy*row - 1] .. start[k + dz*plane + dy*row + 2].
 constexpr int kListCap = 20;
-constexpr float kFilter = 1.0f + 1.0f / 65536.0f;
-
-__device__ __forceinline__ uint32_t run_row_key(const ug_grid_info &g, int bx, int by, int bz,
-                                                int r) {
-    const int dy = r % 3 - 1, dz = r / 3 - 1;
-    return g.box_base + (uint32_t)(((bz + dz) * g.dims[1] + (by + dy)) * g.dims[0] + bx);
-}
+// The filter's relative band on the squared contact distance: the distance s
+// is scaled by c = 1 + 2^-17 (exact in float32, c^2 > 1 + 2^-16), so the
+// band costs no instruction per candidate.  The float32 roundings of d^2 and
+// (c s)^2 stay below 2^-21 relative, far inside it: every pair with
+// d < s passes.
+constexpr float kFilterRoot = 1.0f + 1.0f / 131072.0f;
 
 // The float32 pre-filter of one candidate row q against row i, in Blackwell's
-// packed FP32x2 arithmetic: (dx, dy) = q.xy - p_i.xy and (dz, s) =
-// (q.z, q.w) * (1, 1/2) + (-z_i, r_i + 2m) are one instruction each, the
-// squares two more.  True when |p_i - q|^2 < (r_i + r_q + 2m)^2 (1 + 2^-16).
+// packed FP32x2 arithmetic: (dx, dy) = q.xy - p_i.xy and (dz, c s) =
+// (q.z, q.w) * (1, c/2) + (-z_i, c (r_i + 2m)) are one instruction each, the
+// squares two more.  True when |p_i - q|^2 < c^2 (r_i + r_q + 2m)^2, up to
+// rounding.
 struct FilterRow {
     float2 nxy;   // (-x_i, -y_i)
-    float2 zr;    // (-z_i, r_i + 2m)
+    float2 zr;    // (-z_i, c (r_i + 2m))
 };
 __device__ __forceinline__ FilterRow make_filter_row(const float4 &me, float m2) {
     FilterRow f;
     f.nxy = make_float2(-me.x, -me.y);
-    f.zr = make_float2(-me.z, 0.5f * me.w + m2);
+    f.zr = make_float2(-me.z, (0.5f * me.w + m2) * kFilterRoot);
     return f;
 }
 __device__ __forceinline__ bool prefilter(const float4 &q, const FilterRow &f) {
     const float2 dxy = __fadd2_rn(make_float2(q.x, q.y), f.nxy);
-    const float2 dzs = __ffma2_rn(make_float2(q.z, q.w), make_float2(1.0f, 0.5f), f.zr);
+    const float2 dzs = __ffma2_rn(make_float2(q.z, q.w), make_float2(1.0f, 0.5f * kFilterRoot), f.zr);
     const float2 sxy = __fmul2_rn(dxy, dxy);
     const float2 szs = __fmul2_rn(dzs, dzs);
     const float d2 = sxy.x + sxy.y + szs.x;
-    return d2 < szs.y * kFilter;
+    return d2 < szs.y;
 }
 
 // Visit every candidate j != i of the 27 boxes around row i; `fn(j, row_j)` is

@@ -48,6 +48,38 @@ __device__ __forceinline__ void add_contact(const float4 &me, const float4 &q, f
     ++a.np;
 }
 
+// The float32 pre-filter of one candidate row against both agents of a lane,
+// packed across the two agents (element 0 of each pair is agent 0, element 1
+// agent 1): three differences, the scaled contact distance, the squared
+// centre distance (a multiply and two fused multiply-adds) and the squared
+// contact distance, eight packed operations for both agents where two
+// prefilter() calls take twelve.  Same band as prefilter().
+struct FilterPair {
+    float2 nx, ny, nz, s;
+};
+__device__ __forceinline__ FilterPair make_filter_pair(const float4 &a, const float4 &b, float m2) {
+    FilterPair f;
+    f.nx = make_float2(-a.x, -b.x);
+    f.ny = make_float2(-a.y, -b.y);
+    f.nz = make_float2(-a.z, -b.z);
+    f.s = make_float2((0.5f * a.w + m2) * kFilterRoot, (0.5f * b.w + m2) * kFilterRoot);
+    return f;
+}
+__device__ __forceinline__ void prefilter_pair(const float4 &q, const FilterPair &f, bool &p0,
+                                               bool &p1) {
+    const float2 dx = __fadd2_rn(make_float2(q.x, q.x), f.nx);
+    const float2 dy = __fadd2_rn(make_float2(q.y, q.y), f.ny);
+    const float2 dz = __fadd2_rn(make_float2(q.z, q.z), f.nz);
+    const float h = 0.5f * kFilterRoot;
+    const float2 sv = __ffma2_rn(make_float2(q.w, q.w), make_float2(h, h), f.s);
+    float2 d2 = __fmul2_rn(dx, dx);
+    d2 = __ffma2_rn(dy, dy, d2);
+    d2 = __ffma2_rn(dz, dz, d2);
+    const float2 s2 = __fmul2_rn(sv, sv);
+    p0 = d2.x < s2.x;
+    p1 = d2.y < s2.y;
+}
+
 // Exact contact test and Eq. 1 for the candidates listed since the last flush,
 // warp-converged (every lane calls it; trip count = the warp's longest list).
 // Out of line: the float-float contact test is long and runs a few times per
@@ -124,7 +156,7 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     const bool split = v1 && !mergeable(k0, k1, dx);
     const bool exact_diffs =
         __all_sync(kFull, (!v0 || far_from_origin(me0, g.edge)) && (!v1 || far_from_origin(me1, g.edge)));
-    const FilterRow f0 = make_filter_row(me0, m2), f1 = make_filter_row(me1, m2);
+    const FilterPair fp = make_filter_pair(me0, me1, m2);
     // the force sums are touched only by the flushes: kept in (local) memory
     Accum acc[2] = {{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u}, {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u}};
     int c0 = 0, c1 = 0;
@@ -145,11 +177,13 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
                 const uint32_t jc = index_of(min(t + u, last));
                 const float4 q = __ldg(st + jc);
                 const bool in = t + u < len;
-                if (in & s0 & (jc != i0) & prefilter(q, f0)) {
+                bool p0, p1;
+                prefilter_pair(q, fp, p0, p1);
+                if (in & s0 & (jc != i0) & p0) {
                     w.lst[0][c0][lane] = jc;
                     ++c0;
                 }
-                if (in & s1 & (jc != i1) & prefilter(q, f1)) {
+                if (in & s1 & (jc != i1) & p1) {
                     w.lst[1][c1][lane] = jc;
                     ++c1;
                 }
