@@ -12,12 +12,14 @@
   * a hand-worked grid (edge, padding layer, x-fastest keys, exclusive starts)
     and the uniform grid's completeness condition (Sec. IV-A): every contact
     pair lies in adjacent boxes;
-  * the adjoint against FP64 central finite differences of the forward.
+  * the adjoint against FP64 central finite differences of the forward, on
+    fixtures with capped agents and unmoved agents (one of them with contacts).
 
 Plausible mistakes planted in the oracle (on the CPU) must trip at least one pin
 (test_planted_mistakes_are_caught): in Eq. 1 (a dropped term, a sign, an index,
-the radius), in the displacement (threshold, mass, dt, cap) and in the grid
-(padding, key order, scan).
+the radius), in the displacement (threshold, mass, dt, cap), in the grid
+(padding, key order, scan) and in the adjoint (a sign, the cap projection, the
+adherence mask, the pair Jacobian's transverse part).
 """
 import dataclasses
 import json
@@ -316,9 +318,11 @@ def test_mass_scaling_of_displacement():
 
 
 # ------------------------------------------------------------------ adjoint pins
-def _fd_fixture(seed=5, n=27, steps=3):
+def _fd_fixture(seed=5, n=27, steps=3, still_contact=False):
     """A 3x3x3 jittered lattice whose trajectory keeps every piecewise test
-    (adherence, cap, contact onset) far from its boundary."""
+    (adherence, cap, contact onset) far from its boundary, with capped and
+    unmoved agents; with still_contact=True an unmoved agent that has contacts
+    (its force below the adherence threshold but not zero) in every step."""
     for s in range(seed, seed + 300):
         st = P.jittered_lattice(n, 3, 9.0, 1.5, 9.0, 11.0, s).astype(np.float64)
         prm = O.Params(adherence=0.05, max_disp=0.045)
@@ -332,13 +336,15 @@ def _fd_fixture(seed=5, n=27, steps=3):
             np.fill_diagonal(gap, 1.0)
             ok &= mg["adherence"].min() > 1e-4 and mg["cap"].min() > 1e-4
             ok &= np.abs(gap).min() > 2e-3
+        if still_contact:
+            ok &= all(((~r["moving"]) & (r["npairs"] > 0)).any() for r in recs)
         if ok and any(r["capped"].any() for r in recs) and any((~r["moving"]).any() for r in recs):
             return st, prm
     raise RuntimeError("no FD-safe fixture")
 
 
-def check_adjoint_fd(steps=3):
-    st, prm = _fd_fixture(steps=steps)
+def check_adjoint_fd(steps=3, still_contact=False):
+    st, prm = _fd_fixture(steps=steps, still_contact=still_contact)
     n = len(st)
     target = st[:, :3] + 0.3 * np.sin(np.arange(3 * n).reshape(n, 3))
     res = O.trajectory_grad(st, target, prm, steps, "brute")
@@ -375,11 +381,12 @@ def _loss64(st, target, prm, steps):
         M.Params.as64 = orig
 
 
-def test_adjoint_matches_central_differences():
+@pytest.mark.parametrize("still_contact", [False, True])
+def test_adjoint_matches_central_differences(still_contact):
     orig = M.Params.as64
     try:
         M.Params.as64 = lambda self: self      # FD in FP64 parameters on both sides
-        assert check_adjoint_fd() < 1e-6
+        assert check_adjoint_fd(still_contact=still_contact) < 1e-6
     finally:
         M.Params.as64 = orig
 
@@ -492,6 +499,34 @@ def test_planted_adjoint_mistake_is_caught(monkeypatch):
     assert check_adjoint_fd() < 1e-6
     monkeypatch.setattr(O, "trajectory_grad", bad)
     assert check_adjoint_fd() > 1e-3
+
+
+@pytest.mark.parametrize("which", ["cap_branch_dropped", "adherence_branch_dropped",
+                                   "transverse_term_dropped"])
+def test_planted_reverse_pass_mistakes_are_caught(monkeypatch, which):
+    """Mistakes inside the reverse pass, planted through the forward records it
+    reads (the forward trajectory and the loss are untouched): the cap's
+    projection or the adherence mask forgotten, or the pair Jacobian without
+    its (phi/d)(I - u u^T) part."""
+    monkeypatch.setattr(M.Params, "as64", lambda self: self)
+    assert check_adjoint_fd(still_contact=True) < 1e-6
+    orig = M.trajectory
+
+    def traj(state0, prm=O.Params(), nsteps=1, method="auto", keep=False):
+        out = orig(state0, prm, nsteps, method, keep)
+        if not keep:
+            return out
+        final, recs = out
+        for r in recs:
+            if which == "cap_branch_dropped":
+                r["capped"] = np.zeros_like(r["capped"])
+            elif which == "adherence_branch_dropped":
+                r["moving"] = np.ones_like(r["moving"])
+            else:
+                r["terms"] = dict(r["terms"], phi=np.zeros_like(r["terms"]["phi"]))
+        return final, recs
+    monkeypatch.setattr(M, "trajectory", traj)
+    assert check_adjoint_fd(still_contact=True) > 1e-3
 
 
 def test_sampled_form_equals_full_step():
