@@ -78,6 +78,26 @@ def test_adjoint_small_with_adherence_and_cap(U):
     assert _rel(float(np.sum(dp * v)), fd) < TOL
 
 
+def test_adjoint_unmoved_agent_in_contact(U):
+    """Adherence with contacts: in every step an agent touches others while
+    its force stays below the threshold, so the reverse pass must stop at it
+    (no displacement, no force sensitivity) yet keep its neighbours' pair
+    terms.  GPU gradient = FP64 oracle adjoint on the same float32 rows."""
+    from test_oracle_pins import _fd_fixture
+    st, prm = _fd_fixture(steps=3, still_contact=True)
+    n = len(st)
+    target = st[:, :3] + 0.3 * np.sin(np.arange(3 * n).reshape(n, 3))
+    st32 = st.astype(np.float32)
+    _, recs = O.trajectory(st32, prm, 3, "brute", keep=True)
+    assert all(((~r["moving"]) & (r["npairs"] > 0)).any() for r in recs)
+    ref = O.trajectory_grad(st32, target, prm, 3, "brute")
+    prm_u = U.Params(adherence=prm.adherence, max_disp=prm.max_disp)
+    L, dk, dg, dp, dd = _gpu_grad(U, st32, target, prm_u, 3, 2)
+    assert _rel(L, ref["loss"]) < 1e-5
+    assert _rel(dk, ref["dk"]) < TOL and _rel(dg, ref["dgamma"]) < TOL
+    assert _nrel(dp, ref["dpos"]) < TOL and _nrel(dd, ref["ddiam"]) < TOL
+
+
 def _lattice_case(side, steps):
     st = P.lattice_cube(side, seed=5)
     prm_t = O.Params(k=2.5, gamma=1.2, adherence=0.0)
