@@ -22,6 +22,8 @@
  *   - Agent state is float32, 4 floats per agent: (x, y, z, diameter), 16-byte
  *     aligned.  Forces and gradients use the same 4-float rows.  At most 2^30
  *     agents per call (UG_EINVAL above).
+ *   - max_boxes, the capacity of a box table, lies in [27, 2^31 - 256]
+ *     (UG_EINVAL outside).
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call is
  *     asynchronous: the return value reports argument and launch errors only.
  *     Errors found on the device (bad input values, grid too large, a list

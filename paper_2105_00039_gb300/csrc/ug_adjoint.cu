@@ -223,7 +223,7 @@ int ug_step_backward(const float *ckpt_state, uint32_t n, ug_params p, int32_t n
     }
     if (!ckpt_state || !grad_out || !grad_in || !ws || ((uintptr_t)ws & 255) ||
         ((uintptr_t)ckpt_state & 15) || ((uintptr_t)grad_out & 15) || ((uintptr_t)grad_in & 15) ||
-        max_boxes < 27 || !(p.contact_margin >= 0.0f))
+        max_boxes < 27 || max_boxes > 0x7fffff00u || !(p.contact_margin >= 0.0f))
         return UG_EINVAL;
     AdjLayout L;
     if (adj_layout(ws, n, max_boxes, nsteps, &L) > ws_bytes) return UG_EWORKSPACE;

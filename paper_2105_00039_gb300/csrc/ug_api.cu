@@ -315,7 +315,7 @@ int ug_step_batched(float *state, uint32_t *perm, const uint32_t *sim_offset, ui
     if (n_total == 0 || nsteps == 0) return UG_OK;
     if (n_total > kMaxAgents) return UG_EINVAL;
     if (!rows_ok(state) || !perm || !sim_offset || nsims == 0 || !params || !status || !ws ||
-        !aligned(ws, 256) || max_boxes < 27)
+        !aligned(ws, 256) || max_boxes < 27 || max_boxes > 0x7fffff00u)
         return UG_EINVAL;
     Workspace w;
     if (layout_workspace(ws, n_total, nsims, max_boxes, &w) > ws_bytes) return UG_EWORKSPACE;
@@ -347,7 +347,7 @@ int ug_tune_batched(const float *state, const uint32_t *sim_offset, uint32_t nsi
     if (n_total == 0) return UG_OK;
     if (n_total > kMaxAgents) return UG_EINVAL;
     if (!rows_ok(state) || !sim_offset || nsims == 0 || !params || !ws || !aligned(ws, 256) ||
-        max_boxes < 27)
+        max_boxes < 27 || max_boxes > 0x7fffff00u)
         return UG_EINVAL;
     Workspace w;
     const size_t base = layout_workspace(ws, n_total, nsims, max_boxes, &w);

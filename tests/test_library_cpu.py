@@ -127,3 +127,100 @@ def test_agent_count_limit_without_device(lib):
     assert lib.ug_step(fake, fake, too_many, p, 1, 100, fake, 1 << 62, fake, None) == -1
     lib.ug_iota.argtypes = [P, ctypes.c_uint32, P]
     assert lib.ug_iota(fake, too_many, None) == -1
+
+
+def test_every_entry_point_validates_without_device():
+    """Each call below fails its host-side checks (or is a documented no-op)
+    before any device work: fake but aligned pointers, one bad argument each."""
+    from paper_2105_00039_gb300 import ugmech as U
+    lib = U.load()
+    P = ctypes.c_void_p
+    p = U.Params().c()
+    neg = U.Params(contact_margin=-1.0).c()
+    fake = P(0x10000)
+    odd = P(0x10008)                  # 8-byte aligned only
+    big = 1 << 62                     # workspace size that passes every size check
+    over = 0x7fffff01                 # max_boxes above 2^31 - 256
+    too_many = (1 << 30) + 1
+    EINVAL, EWORKSPACE = U.UG_EINVAL, U.UG_EWORKSPACE
+
+    # forces, pairs, displacement
+    assert lib.ug_compute_forces(None, None, None, 0, p, None, None, None) == 0
+    assert lib.ug_compute_forces(fake, fake, fake, too_many, p, fake, fake, None) == EINVAL
+    assert lib.ug_compute_forces(odd, fake, fake, 10, p, fake, fake, None) == EINVAL
+    assert lib.ug_compute_forces(fake, None, fake, 10, p, fake, fake, None) == EINVAL
+    assert lib.ug_compute_forces(fake, fake, fake, 10, p, odd, fake, None) == EINVAL
+    assert lib.ug_compute_forces(fake, fake, fake, 10, p, fake, None, None) == EINVAL
+    assert lib.ug_list_pairs(fake, fake, fake, 10, 0.0, 8, fake, None, fake, None) == EINVAL
+    assert lib.ug_list_pairs(fake, fake, fake, 10, 0.0, 0, None, None, fake, None) == EINVAL
+    assert lib.ug_apply_displacement(fake, fake, 10, p, fake, odd, fake, None) == EINVAL
+    assert lib.ug_apply_displacement(fake, fake, 10, p, None, None, fake, None) == EINVAL
+
+    # grid build
+    gb = lambda mb, m, bs: lib.ug_grid_build(fake, None, 10, m, fake, fake, bs, mb, fake, fake,
+                                             big, fake, None)
+    assert gb(over, 0.0, fake) == EINVAL
+    assert gb(100, -1.0, fake) == EINVAL
+    assert gb(100, 0.0, P(0x10004)) == EINVAL          # box table not 16-byte aligned
+
+    # fused steps
+    for step in (lib.ug_step, lib.ug_step_pairs_once):
+        assert step(fake, fake, 10, p, -1, 100, fake, big, fake, None) == EINVAL
+        assert step(fake, fake, 10, p, 1, 26, fake, big, fake, None) == EINVAL
+        assert step(fake, fake, 10, p, 1, over, fake, big, fake, None) == EINVAL
+        assert step(fake, fake, 10, neg, 1, 100, fake, big, fake, None) == EINVAL
+        assert step(fake, fake, 10, p, 1, 100, odd, big, fake, None) == EINVAL   # ws alignment
+        assert step(fake, fake, 10, p, 1, 100, fake, 16, fake, None) == EWORKSPACE
+    events = (ctypes.c_void_p * 6)()
+    assert lib.ug_step_traced(fake, fake, 10, p, 1, 100, fake, big, fake, None, None, 7) == EINVAL
+    assert lib.ug_step_traced(fake, fake, 10, p, 1, 100, fake, big, fake, None, events, 6) == EINVAL
+
+    # batched and its tuner
+    def tuning(block, apl, mode):
+        t = U.ug_tuning()
+        t.sweep_block, t.agents_per_lane, t.pair_mode = block, apl, mode
+        return ctypes.byref(t)
+    sb = lambda mb, t: lib.ug_step_batched(fake, fake, fake, 2, 10, fake, 1, mb, t, fake, big,
+                                           fake, None)
+    assert sb(over, None) == EINVAL
+    assert sb(100, tuning(96, 2, 0)) == EINVAL
+    assert sb(100, tuning(128, 3, 0)) == EINVAL
+    assert sb(100, tuning(128, 2, 2)) == EINVAL
+    assert lib.ug_step_batched(fake, fake, fake, 2, 10, fake, 1, 100, None, fake, 16, fake,
+                               None) == EWORKSPACE
+    best = U.ug_tuning()
+    assert lib.ug_tune_batched(fake, fake, 2, 10, fake, 100, None, fake, big, None) == EINVAL
+    assert lib.ug_tune_batched(None, None, 0, 0, None, 0, ctypes.byref(best), None, 0, None) == 0
+    assert (best.sweep_block, best.agents_per_lane, best.pair_mode) == (128, 2, 0)
+    assert lib.ug_tune_batched(fake, fake, 0, 10, fake, 100, ctypes.byref(best), fake, big,
+                               None) == EINVAL
+    assert lib.ug_tune_batched(fake, fake, 2, 10, fake, over, ctypes.byref(best), fake, big,
+                               None) == EINVAL
+    assert lib.ug_tune_batched(fake, fake, 2, 10, fake, 100, ctypes.byref(best), fake, 16,
+                               None) == EWORKSPACE
+
+    # adjoint (n > 0 and nsteps > 0 throughout: the zero cases touch the device)
+    bw = lambda ck, mb, prm, ws_bytes, gp=fake, st=fake: lib.ug_step_backward(
+        ck, 10, prm, 2, mb, fake, fake, gp, fake, ws_bytes, st, None)
+    assert lib.ug_step_backward(fake, 10, p, -1, 100, fake, fake, fake, fake, big, fake,
+                                None) == EINVAL
+    assert bw(fake, 100, p, big, gp=None) == EINVAL
+    assert bw(fake, 100, p, big, st=None) == EINVAL
+    assert bw(odd, 100, p, big) == EINVAL
+    assert bw(fake, 26, p, big) == EINVAL
+    assert bw(fake, over, p, big) == EINVAL
+    assert bw(fake, 100, neg, big) == EINVAL
+    assert bw(fake, 100, p, 16) == EWORKSPACE
+
+    # every pair once, forces only
+    fs = lambda ws, ws_bytes: lib.ug_forces_symmetric(1, fake, fake, fake, 10, p, fake, ws,
+                                                      ws_bytes, fake, None)
+    assert fs(odd, big) == EINVAL
+    assert fs(fake, 32 * 10 - 1) == EWORKSPACE
+
+    # row reordering helpers
+    for fn in (lib.ug_scatter_rows, lib.ug_gather_rows):
+        assert fn(odd, fake, 10, fake, None) == EINVAL
+        assert fn(fake, None, 10, fake, None) == EINVAL
+        assert fn(fake, fake, 10, odd, None) == EINVAL
+        assert fn(fake, fake, too_many, fake, None) == EINVAL
