@@ -341,10 +341,12 @@ def apply_displacement(state, force, params: Params = Params(), out=None, want_d
 
 
 class Stepper:
-    """Holds the workspace for repeated fused steps on one population size.
+    """Holds the workspace for repeated fused steps on populations of up to n
+    agents (and up to nsims simulations, max_boxes boxes in total).
 
-    step() advances `state` (n, 4) and `perm` (n,) in place; both stay on the
-    device in box order.  Calls are asynchronous; status is checked on demand."""
+    step() advances `state` (m, 4) and `perm` (m,) in place, m <= n; both stay
+    on the device in box order.  Calls are asynchronous; status is checked on
+    demand."""
 
     def __init__(self, n: int, max_boxes: int, device, nsims: int = 1):
         self.lib = load()
@@ -352,13 +354,20 @@ class Stepper:
         self.ws = workspace(self.lib.ug_workspace_bytes(self.n, self.nsims, self.max_boxes), device)
         self.status = new_status(device)
 
+    def _agents(self, state, perm) -> int:
+        _rows(state, "state")
+        m = state.shape[0]
+        if m > self.n:
+            raise ValueError(f"state has {m} rows; this Stepper has room for {self.n}")
+        _ids(perm, m, "perm")
+        return m
+
     def step(self, state, perm, params: Params, nsteps: int = 1, pairs_once: bool = False):
         """nsteps fused steps; pairs_once selects ug_step_pairs_once (each pair
         evaluated once, faster on dense grids)."""
-        _rows(state, "state")
-        _ids(perm, self.n, "perm")
+        m = self._agents(state, perm)
         fn = self.lib.ug_step_pairs_once if pairs_once else self.lib.ug_step
-        rc = fn(_ptr(state), _ptr(perm), self.n, params.c(), int(nsteps), self.max_boxes,
+        rc = fn(_ptr(state), _ptr(perm), m, params.c(), int(nsteps), self.max_boxes,
                 _ptr(self.ws), self.ws.numel(), _ptr(self.status), _stream())
         _check(rc, "ug_step_pairs_once" if pairs_once else "ug_step")
 
@@ -366,20 +375,23 @@ class Stepper:
         """step() with caller-created torch.cuda.Event objects recorded between
         kernels (len(events) >= 2 + 5 * nsteps; each must have been recorded once
         so that its CUDA handle exists)."""
-        _rows(state, "state")
-        _ids(perm, self.n, "perm")
+        m = self._agents(state, perm)
         arr = (ctypes.c_void_p * len(events))(*[ctypes.c_void_p(e.cuda_event) for e in events])
-        rc = self.lib.ug_step_traced(_ptr(state), _ptr(perm), self.n, params.c(), int(nsteps),
+        rc = self.lib.ug_step_traced(_ptr(state), _ptr(perm), m, params.c(), int(nsteps),
                                      self.max_boxes, _ptr(self.ws), self.ws.numel(),
                                      _ptr(self.status), _stream(), arr, len(events))
         _check(rc, "ug_step_traced")
 
     def step_batched(self, state, perm, sim_offset, params_dev, nsteps: int = 1,
                      tuning: ug_tuning | None = None):
-        _rows(state, "state")
-        _ids(perm, self.n, "perm")
+        """nsteps fused steps of every simulation: sim_offset (nsims + 1,) int32
+        on the device, sim_offset[nsims] = number of rows; params_dev (nsims, 7)."""
+        m = self._agents(state, perm)
+        if sim_offset.numel() != self.nsims + 1 or params_dev.shape[0] != self.nsims:
+            raise ValueError(f"sim_offset needs {self.nsims + 1} entries and params_dev "
+                             f"{self.nsims} rows")
         rc = self.lib.ug_step_batched(_ptr(state), _ptr(perm), _ptr(sim_offset), self.nsims,
-                                      self.n, _ptr(params_dev), int(nsteps), self.max_boxes,
+                                      m, _ptr(params_dev), int(nsteps), self.max_boxes,
                                       ctypes.byref(tuning) if tuning is not None else None,
                                       _ptr(self.ws), self.ws.numel(), _ptr(self.status),
                                       _stream())
@@ -496,7 +508,12 @@ def step_backward(ckpt_state, params: Params, nsteps: int, max_boxes: int, grad_
 
 
 def tune_batched(state, sim_offset, params_dev, nsims: int, max_boxes: int) -> ug_tuning:
+    """The fastest (sweep_block, agents_per_lane, pair_mode) for these
+    simulations, timed on scratch copies of the rows (state is only read)."""
     lib = load()
+    _rows(state, "state")
+    if sim_offset.numel() != nsims + 1 or params_dev.shape[0] != nsims:
+        raise ValueError(f"sim_offset needs {nsims + 1} entries and params_dev {nsims} rows")
     n = state.shape[0]
     ws = workspace(lib.ug_workspace_bytes(n, nsims, max_boxes) + 20 * n + 1024, state.device)
     best = ug_tuning()

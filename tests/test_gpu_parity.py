@@ -598,6 +598,29 @@ def test_pairs_once_step_against_oracle(U, name):
 
 
 @pytest.mark.parametrize("pairs_once", [False, True])
+def test_stepper_room_serves_smaller_populations(U, pairs_once):
+    """A Stepper sized for n agents steps any population of up to n (agents
+    added or removed between calls), with the same bits as one sized exactly,
+    and refuses a larger one before any device work."""
+    st = P.small_uniform(4)
+    big = U.Stepper(len(st), 200000, torch.device(DEV))
+    for m in (3000, 4096, 1234):
+        part = st[:m]
+        x = _gpu(part)
+        perm = U.iota(m, x.device)
+        big.step(x, perm, U.Params(), 3, pairs_once=pairs_once)
+        big.check()
+        ref, pref = _run_steps(U, part, U.Params(), 3, max_boxes=200000, pairs_once=pairs_once)
+        assert np.array_equal(x.cpu().numpy(), ref) and np.array_equal(perm.cpu().numpy(), pref)
+    small = U.Stepper(100, 200000, torch.device(DEV))
+    x = _gpu(st[:101])
+    with pytest.raises(ValueError):
+        small.step(x, U.iota(101, x.device), U.Params(), 1)
+    with pytest.raises(ValueError):
+        small.step(_gpu(st[:50]), U.iota(60, x.device), U.Params(), 1)
+
+
+@pytest.mark.parametrize("pairs_once", [False, True])
 def test_simulation_run_host_to_host(U, pairs_once):
     """The end-to-end API: host rows in id order in, host rows in id order out,
     the same bits as the device-side steps."""
