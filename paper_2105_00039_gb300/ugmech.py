@@ -155,17 +155,67 @@ def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def _rows(t: torch.Tensor, name: str) -> torch.Tensor:
-    if not (t.is_cuda and t.dtype == torch.float32 and t.dim() == 2 and t.shape[1] == 4
-            and t.is_contiguous()):
-        raise ValueError(f"{name} must be a contiguous CUDA float32 tensor of shape (n, 4)")
+# Argument checks.  Every tensor handed to the library is checked for dtype,
+# layout and size against the others before any call, so that no kernel reads
+# or writes past a buffer; the device is checked last (one helper, _on_gpu).
+def _on_gpu(t: torch.Tensor) -> bool:
+    return t.is_cuda
+
+
+def _device(t: torch.Tensor, name: str, device=None):
+    if not _on_gpu(t):
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, the other arguments on {device}")
+
+
+def _rows(t: torch.Tensor, name: str, n: int | None = None, device=None) -> torch.Tensor:
+    if not (t.dtype == torch.float32 and t.dim() == 2 and t.shape[1] == 4 and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float32 tensor of shape (n, 4)")
+    if n is not None and t.shape[0] != n:
+        raise ValueError(f"{name} must have {n} rows, not {t.shape[0]}")
+    _device(t, name, device)
     return t
 
 
-def _ids(t: torch.Tensor, n: int, name: str) -> torch.Tensor:
-    if not (t.is_cuda and t.dtype == torch.int32 and t.numel() == n and t.is_contiguous()):
-        raise ValueError(f"{name} must be a contiguous CUDA int32 tensor with {n} entries")
+def _ids(t: torch.Tensor, n: int, name: str, device=None) -> torch.Tensor:
+    if not (t.dtype == torch.int32 and t.numel() == n and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous int32 tensor with {n} entries")
+    _device(t, name, device)
     return t
+
+
+def _buf(t: torch.Tensor, dtype, numel: int, name: str, device, exact: bool = False):
+    """A contiguous buffer of `dtype` with at least (or, exact, exactly) `numel` entries."""
+    ok = t.dtype == dtype and t.is_contiguous() and (t.numel() == numel if exact else
+                                                     t.numel() >= numel)
+    if not ok:
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor with "
+                         f"{'' if exact else 'at least '}{numel} entries")
+    _device(t, name, device)
+    return t
+
+
+def _grid(box_start: torch.Tensor, info: torch.Tensor, device):
+    """The box table and grid record of grid_build: int32 [max_boxes + 1], 48 bytes."""
+    _buf(box_start, torch.int32, 28, "box_start", device)
+    _buf(info, torch.uint8, 48, "info", device)
+
+
+def _batch(sim_offset: torch.Tensor, params_dev: torch.Tensor, nsims: int, device):
+    """Per-simulation arguments of the batched calls: int32 [nsims + 1] offsets
+    and float32 [nsims, 7] parameter rows, on the rows' device."""
+    _buf(sim_offset, torch.int32, nsims + 1, "sim_offset", device, exact=True)
+    if not (params_dev.dtype == torch.float32 and params_dev.dim() == 2 and
+            tuple(params_dev.shape) == (nsims, 7) and params_dev.is_contiguous()):
+        raise ValueError(f"params_dev must be a contiguous float32 tensor of shape ({nsims}, 7)")
+    _device(params_dev, "params_dev", device)
+
+
+def _status(status: torch.Tensor | None, device) -> torch.Tensor:
+    if status is None:
+        return new_status(device)
+    return _buf(status, torch.int32, 1, "status", device)
 
 
 def _check(rc: int, where: str):
@@ -230,7 +280,8 @@ def grid_build(state: torch.Tensor, perm_in: torch.Tensor | None = None,
     n = state.shape[0]
     dev = state.device
     if perm_in is not None:
-        _ids(perm_in, n, "perm_in")
+        _ids(perm_in, n, "perm_in", dev)
+    status = _status(status, dev)
     if max_boxes is None:
         max_boxes = estimate_max_boxes(state, contact_margin, slack=1.0)
     st_sorted = torch.empty_like(state)
@@ -238,7 +289,6 @@ def grid_build(state: torch.Tensor, perm_in: torch.Tensor | None = None,
     box_start = torch.zeros(max_boxes + 1, dtype=torch.int32, device=dev)
     info = torch.zeros(48, dtype=torch.uint8, device=dev)
     ws = workspace(lib.ug_workspace_bytes(n, 1, max_boxes), dev)
-    status = new_status(dev) if status is None else status
     rc = lib.ug_grid_build(_ptr(state), _ptr(perm_in), n, float(contact_margin), _ptr(st_sorted),
                            _ptr(perm_sorted), _ptr(box_start), max_boxes, _ptr(info), _ptr(ws),
                            ws.numel(), _ptr(status), _stream())
@@ -254,8 +304,9 @@ def compute_forces(state_sorted, box_start, info, params: Params = Params(), sta
     lib = load()
     _rows(state_sorted, "state_sorted")
     n = state_sorted.shape[0]
+    _grid(box_start, info, state_sorted.device)
+    status = _status(status, state_sorted.device)
     force = torch.empty_like(state_sorted)
-    status = new_status(state_sorted.device) if status is None else status
     rc = lib.ug_compute_forces(_ptr(state_sorted), _ptr(box_start), _ptr(info), n, params.c(),
                                _ptr(force), _ptr(status), _stream())
     _check(rc, "ug_compute_forces")
@@ -270,9 +321,10 @@ def list_pairs(state_sorted, box_start, info, contact_margin: float = 0.0,
     lib = load()
     _rows(state_sorted, "state_sorted")
     n = state_sorted.shape[0]
+    _grid(box_start, info, state_sorted.device)
+    status = _status(status, state_sorted.device)
     count = torch.empty(n, dtype=torch.int32, device=state_sorted.device)
     nbr = torch.full((n, max_per_agent), -1, dtype=torch.int32, device=state_sorted.device)
-    status = new_status(state_sorted.device) if status is None else status
     rc = lib.ug_list_pairs(_ptr(state_sorted), _ptr(box_start), _ptr(info), n,
                            float(contact_margin), max_per_agent, _ptr(count), _ptr(nbr),
                            _ptr(status), _stream())
@@ -290,9 +342,10 @@ def forces_symmetric(state_sorted, box_start, info, params: Params = Params(),
     lib = load()
     _rows(state_sorted, "state_sorted")
     n = state_sorted.shape[0]
+    _grid(box_start, info, state_sorted.device)
+    status = _status(status, state_sorted.device)
     force = torch.empty_like(state_sorted)
     ws = workspace(32 * n + 256, state_sorted.device)
-    status = new_status(state_sorted.device) if status is None else status
     rc = lib.ug_forces_symmetric(int(bool(each_pair_once)), _ptr(state_sorted), _ptr(box_start),
                                  _ptr(info), n, params.c(), _ptr(force), _ptr(ws), ws.numel(),
                                  _ptr(status), _stream())
@@ -313,7 +366,7 @@ def forces_ladder(state, version: int, params: Params = Params(), max_boxes: int
         max_boxes = estimate_max_boxes(state, params.contact_margin)
     ws = workspace(lib.ug_ladder_workspace_bytes(n, max_boxes), state.device)
     force = torch.empty((n, 4), dtype=torch.float64, device=state.device)
-    status = new_status(state.device) if status is None else status
+    status = _status(status, state.device)
     rc = lib.ug_forces_ladder(int(version), _ptr(state), n, params.c(), max_boxes, _ptr(force),
                               _ptr(ws), ws.numel(), _ptr(status), _stream())
     _check(rc, "ug_forces_ladder")
@@ -327,11 +380,12 @@ def apply_displacement(state, force, params: Params = Params(), out=None, want_d
     """Adherence, integration and cap (Sec. III): returns (new_state, disp)."""
     lib = load()
     _rows(state, "state")
-    _rows(force, "force")
     n = state.shape[0]
-    out = torch.empty_like(state) if out is None else out
+    dev = state.device
+    _rows(force, "force", n, dev)
+    out = torch.empty_like(state) if out is None else _rows(out, "out", n, dev)
     disp = torch.empty_like(state) if want_disp else None
-    status = new_status(state.device) if status is None else status
+    status = _status(status, dev)
     rc = lib.ug_apply_displacement(_ptr(state), _ptr(force), n, params.c(), _ptr(out), _ptr(disp),
                                    _ptr(status), _stream())
     _check(rc, "ug_apply_displacement")
@@ -360,6 +414,8 @@ class Stepper:
         if m > self.n:
             raise ValueError(f"state has {m} rows; this Stepper has room for {self.n}")
         _ids(perm, m, "perm")
+        _device(state, "state", self.ws.device)
+        _device(perm, "perm", self.ws.device)
         return m
 
     def step(self, state, perm, params: Params, nsteps: int = 1, pairs_once: bool = False):
@@ -387,9 +443,7 @@ class Stepper:
         """nsteps fused steps of every simulation: sim_offset (nsims + 1,) int32
         on the device, sim_offset[nsims] = number of rows; params_dev (nsims, 7)."""
         m = self._agents(state, perm)
-        if sim_offset.numel() != self.nsims + 1 or params_dev.shape[0] != self.nsims:
-            raise ValueError(f"sim_offset needs {self.nsims + 1} entries and params_dev "
-                             f"{self.nsims} rows")
+        _batch(sim_offset, params_dev, self.nsims, self.ws.device)
         rc = self.lib.ug_step_batched(_ptr(state), _ptr(perm), _ptr(sim_offset), self.nsims,
                                       m, _ptr(params_dev), int(nsteps), self.max_boxes,
                                       ctypes.byref(tuning) if tuning is not None else None,
@@ -410,6 +464,7 @@ def iota(n: int, device) -> torch.Tensor:
 def scatter_rows(rows, perm):
     """rows_by_id[perm[s]] = rows[s]."""
     _rows(rows, "rows")
+    _ids(perm, rows.shape[0], "perm", rows.device)
     out = torch.empty_like(rows)
     _check(load().ug_scatter_rows(_ptr(rows), _ptr(perm), rows.shape[0], _ptr(out), _stream()),
            "ug_scatter_rows")
@@ -419,6 +474,7 @@ def scatter_rows(rows, perm):
 def gather_rows(rows_by_id, perm):
     """rows[s] = rows_by_id[perm[s]]."""
     _rows(rows_by_id, "rows_by_id")
+    _ids(perm, rows_by_id.shape[0], "perm", rows_by_id.device)
     out = torch.empty_like(rows_by_id)
     _check(load().ug_gather_rows(_ptr(rows_by_id), _ptr(perm), rows_by_id.shape[0], _ptr(out),
                                  _stream()), "ug_gather_rows")
@@ -492,14 +548,16 @@ def step_backward(ckpt_state, params: Params, nsteps: int, max_boxes: int, grad_
     """dL/d(ckpt rows) and (dL/dk, dL/dgamma) for nsteps steps from ckpt_state."""
     lib = load()
     _rows(ckpt_state, "ckpt_state")
-    _rows(grad_out, "grad_out")
     n = ckpt_state.shape[0]
     dev = ckpt_state.device
+    _rows(grad_out, "grad_out", n, dev)
+    status = _status(status, dev)
     if ws is None:
         ws = workspace(lib.ug_backward_workspace_bytes(n, max_boxes, nsteps), dev)
+    else:
+        _buf(ws, torch.uint8, 256, "ws", dev)
     grad_in = torch.empty_like(ckpt_state)
     gp = torch.zeros(2, dtype=torch.float32, device=dev)
-    status = new_status(dev) if status is None else status
     rc = lib.ug_step_backward(_ptr(ckpt_state), n, params.c(), int(nsteps), max_boxes,
                               _ptr(grad_out), _ptr(grad_in), _ptr(gp), _ptr(ws), ws.numel(),
                               _ptr(status), _stream())
@@ -512,8 +570,7 @@ def tune_batched(state, sim_offset, params_dev, nsims: int, max_boxes: int) -> u
     simulations, timed on scratch copies of the rows (state is only read)."""
     lib = load()
     _rows(state, "state")
-    if sim_offset.numel() != nsims + 1 or params_dev.shape[0] != nsims:
-        raise ValueError(f"sim_offset needs {nsims + 1} entries and params_dev {nsims} rows")
+    _batch(sim_offset, params_dev, nsims, state.device)
     n = state.shape[0]
     ws = workspace(lib.ug_workspace_bytes(n, nsims, max_boxes) + 20 * n + 1024, state.device)
     best = ug_tuning()
