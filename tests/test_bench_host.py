@@ -59,3 +59,56 @@ def test_clock_samples_are_summarised():
     assert "hw_slowdown" in c.summary()["reasons"]
     c.lines = []
     assert c.summary()["reasons"] == ["unsampled"]
+
+
+def _json_lines(text):
+    import json
+    out = []
+    for ln in text.splitlines():
+        ln = ln.strip()
+        if ln.startswith("{"):
+            out.append(json.loads(ln))
+    return out
+
+
+def _check_reference_line(d, n_gpus):
+    assert d["impl"] == "reference" and d["metric"] == "agent-steps/s"
+    assert d["unit"] == "agent-steps/s" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["n_gpus"] == n_gpus and d["steps"] == 1 and d["warmup"] == 0
+    assert d["vs_baseline"] is None and d["dtype"] == "f64" and d["data"] == "synthetic"
+    assert d["ms_per_step"] > 0 and "workload" in d["config"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    e2e = d["e2e"]
+    assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference: the oracle timed on the host cores, one JSON
+    line with the keys the benchmark contract asks for."""
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "0"], cwd=ROOT, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = _json_lines(r.stdout)
+    assert len(lines) == 1
+    _check_reference_line(lines[0], 1)
+
+
+def test_reference_arm_under_torchrun_two_ranks():
+    """Launched like the multi-GPU runs (torchrun, two ranks, gloo on the host):
+    rank 0 alone times the oracle and prints the line; the other rank exits 0
+    without work."""
+    import subprocess
+    port = 30500 + os.getpid() % 1000
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(port),
+           os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2", "--steps", "1",
+           "--warmup", "0"]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = _json_lines(r.stdout)
+    assert len(lines) == 1
+    _check_reference_line(lines[0], 2)
