@@ -49,6 +49,26 @@ SWEEP_DRAM_BYTES = 23.521792e6 + 0.320256e6
 SWEEP_DRAM_BYTES_SRC = "9b362eb61c0f7119"      # sha256[:16] of ug_sweep2.cu + ug_internal.cuh when captured
 
 
+# Warp instructions of one k_sweep2 launch on this workload, from the same ncu
+# capture (and valid under the same source check) as the DRAM bytes above, and
+# the SMs' issue limit: one warp instruction per scheduler per clock, four
+# schedulers per SM.
+SWEEP_WARP_INST = 89_700_118
+ISSUE_PEAK_GINST_S = 152 * 4 * 2.07
+
+
+def issue_roofline(avg_launch_ms: float):
+    """The sweep against the instruction-issue limit (the bound that holds it),
+    or None once its source has changed since the instruction count was taken."""
+    if sweep_traffic() is None:
+        return None
+    achieved = SWEEP_WARP_INST / (avg_launch_ms / 1000.0) / 1e9
+    return {"warp_inst_per_launch": SWEEP_WARP_INST, "achieved_ginst_s": achieved,
+            "peak_ginst_s": ISSUE_PEAK_GINST_S, "frac": achieved / ISSUE_PEAK_GINST_S,
+            "peak_source": "derived: 152 SMs x 4 schedulers x 1 warp instruction per clock "
+                           "x 2.07 GHz; instructions per launch from ncu"}
+
+
 def sweep_traffic():
     """The captured DRAM bytes if the sweep's source is unchanged since, else None."""
     import hashlib
@@ -322,6 +342,7 @@ def run_ours(args, world, rank, local, pg):
                      "candidates_per_agent": cand, "contacts_per_agent": cont,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                      "note": "instruction issue: 68% of issue slots busy, 89.7M warp instructions per launch (ncu), see profiles/k_sweep2_lattice1m.md",
+                     "issue": issue_roofline(avg_launch_ms) if dom == "sweep" else None,
                      "hbm": {"achieved_gbs": achieved, "peak_gbs": hbm, "frac": achieved / hbm,
                              "alg_bytes_per_launch": alg_bytes,
                              "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},

@@ -112,3 +112,14 @@ def test_reference_arm_under_torchrun_two_ranks():
     lines = _json_lines(r.stdout)
     assert len(lines) == 1
     _check_reference_line(lines[0], 2)
+
+
+def test_issue_roofline(monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.issue_roofline(0.1)                      # 100 us per launch
+    assert r is not None, "the sweep's source changed since its ncu capture"
+    assert abs(r["achieved_ginst_s"] - bench.SWEEP_WARP_INST / 1e-4 / 1e9) < 1e-6
+    assert abs(r["frac"] - r["achieved_ginst_s"] / (152 * 4 * 2.07)) < 1e-12
+    monkeypatch.setattr(bench, "sweep_traffic", lambda: None)
+    assert bench.issue_roofline(0.1) is None
