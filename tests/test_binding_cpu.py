@@ -63,17 +63,23 @@ def test_valid_calls_reach_the_library_with_their_sizes(rec):
     sp = U.Stepper(10, 100, torch.device("cpu"), nsims=2)
     sp.step(_rows(7), _ids(7), U.Params(), 1)
     sp.step(_rows(10), _ids(10), U.Params(), 1, pairs_once=True)
+
+    class _Event:
+        cuda_event = 0
+    sp.step_traced(_rows(9), _ids(9), U.Params(), 1, [_Event()] * 7)
     sp.step_batched(_rows(10), _ids(10), torch.tensor([0, 4, 10], dtype=torch.int32),
                     torch.zeros(2, 7), 1)
     U.tune_batched(st, torch.tensor([0, 4, 10], dtype=torch.int32), torch.zeros(2, 7), 2, 100)
     names = [c[0] for c in rec.calls]
     for fn in ("ug_grid_build", "ug_compute_forces", "ug_list_pairs", "ug_forces_symmetric",
                "ug_forces_ladder", "ug_apply_displacement", "ug_scatter_rows", "ug_gather_rows",
-               "ug_step_backward", "ug_step", "ug_step_pairs_once", "ug_step_batched",
-               "ug_tune_batched"):
+               "ug_step_backward", "ug_step", "ug_step_pairs_once", "ug_step_traced",
+               "ug_step_batched", "ug_tune_batched"):
         assert fn in names, fn
     steps = [c[1] for c in rec.calls if c[0] in ("ug_step", "ug_step_pairs_once")]
     assert [a[2] for a in steps] == [7, 10]           # the rows given, not the room held
+    traced = [c[1] for c in rec.calls if c[0] == "ug_step_traced"]
+    assert traced[0][2] == 9 and traced[0][-1] == 7
 
 
 @pytest.mark.parametrize("case", [
