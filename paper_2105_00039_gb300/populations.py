@@ -135,7 +135,8 @@ def batched_population(nsims: int = 256, nmin: int = 1000, nmax: int = 200_000,
 
 
 def random_unit_vectors(n: int, seed: int) -> np.ndarray:
-    """n float64 unit vectors (for directional-derivative checks)."""
+    """One random direction over n agents' positions: an (n, 3) float64 array of
+    unit (Frobenius) norm, for directional-derivative checks."""
     g = np.stack([uniform01(seed, 201 + a, n) for a in range(3)], axis=1) * 2.0 - 1.0
     g /= np.linalg.norm(g)
     return g
