@@ -237,7 +237,8 @@ def check_status(status: torch.Tensor, where: str = "device"):
 def workspace(nbytes: int, device) -> torch.Tensor:
     """A 256-byte aligned byte buffer (torch's allocator aligns to 512)."""
     t = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
-    assert t.data_ptr() % 256 == 0
+    if t.data_ptr() % 256:
+        raise RuntimeError("workspace allocation is not 256-byte aligned")
     return t
 
 
