@@ -154,12 +154,15 @@ int ug_grid_build(const float *state_in, const uint32_t *perm_in, uint32_t n,
  * fixed memory budget -- so they cannot supply ug_grid_build's workspace.  This
  * variant uses a fixed scratch array of about 7 MiB compiled into the library
  * (one per GPU that loads it, held until the process exits) and calls no
- * allocator.  Arguments and results are those of ug_grid_build.
- *   Limits: n <= 262144 and max_boxes <= 1048576, else UG_EWORKSPACE (the
- *   built-in scratch is too small) before any device work.
- *   The first call on a device looks up the array's address; make it before
- *   any stream capture.  Every call shares the array: calls that overlap on the
- *   GPU (other streams or host threads on the same device) race on it. */
+ * allocator.  Arguments and results are those of ug_grid_build, and its
+ * argument checks come first (UG_EINVAL as there).
+ *   Limits, checked after them: n <= 262144 and max_boxes <= 1048576, else
+ *   UG_EWORKSPACE (the built-in scratch is too small) before any device work.
+ *   The first call in a CUDA context looks up the array's address in that
+ *   context (again after cudaDeviceReset, or in a context other than the
+ *   device's primary one); make it before any stream capture.  Every call
+ *   shares the array: calls that overlap on the GPU (other streams or host
+ *   threads on the same device) race on it. */
 int ug_grid_build_noalloc(const float *state_in, const uint32_t *perm_in, uint32_t n,
                           float contact_margin, float *state_sorted, uint32_t *perm_sorted,
                           uint32_t *box_start, uint32_t max_boxes, ug_grid_info *info,

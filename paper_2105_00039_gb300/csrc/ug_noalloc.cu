@@ -8,13 +8,17 @@
 // ug_grid_build asks for, so this variant brings its own.
 //
 // The array (kScratchBytes, about 7 MiB) is a file-scope __device__ variable:
-// every GPU that loads the library holds one copy until the process exits.  The
-// first call on a device looks up the array's device address with
-// cudaGetSymbolAddress (once per device, with that device current); make that
-// first call before any stream capture.  All calls share the one array and it
-// keeps the previous call's contents, so the parts that must start at zero are
-// cleared on every call, and calls that overlap on the GPU (different streams,
-// or different host threads on one device) race on it.
+// every GPU that loads the library holds one copy until the process exits.  Its
+// device address is looked up with cudaGetSymbolAddress the first time a call
+// runs in a given CUDA context (with that context's device current) and cached
+// under the context's unique id, so a call made after cudaDeviceReset, or in a
+// context other than the device's primary one, looks the address up again
+// rather than reuse one that belonged to a context that is gone.  Make the
+// first call in a context before any stream capture.  All calls share the one
+// array and it keeps the previous call's contents, so the parts that must start
+// at zero are cleared on every call, and calls that overlap on the GPU
+// (different streams, or different host threads on one device) race on it.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -28,32 +32,79 @@ constexpr uint32_t kNoAllocMaxBoxes = 1u << 20;    // 1,048,576 grid boxes
 constexpr size_t kAlign = 256;
 constexpr size_t up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 constexpr size_t kNoAllocTiles = (kNoAllocMaxBoxes + ug::kScanTile - 1) / ug::kScanTile;
-// ctrl | tile sums | counts | bounds (these four are zeroed per call) | key | rank | tmp
-constexpr size_t kOffTiles = up(sizeof(ug::Ctrl));
-constexpr size_t kOffCounts = kOffTiles + up(4ull * ug::kTileSumStride * ug::kTileCopies * kNoAllocTiles);
-constexpr size_t kOffBounds = kOffCounts + up(4ull * kNoAllocMaxBoxes);
-constexpr size_t kOffKey = kOffBounds + up(4ull * ug::kBoundsWords * ug::kBoundsCopiesSingle);
+// ctrl | bounds | tile sums | counts | key | rank | tmp.  Every call clears the
+// control words, the bounds, the tile sums of its own scan tiles and the counts
+// of its own max_boxes boxes; the rest is written before it is read.
+constexpr size_t kOffBounds = up(sizeof(ug::Ctrl));
+constexpr size_t kOffTiles = kOffBounds + up(4ull * ug::kBoundsWords * ug::kBoundsCopiesSingle);
+constexpr size_t kTileBytes = 4ull * ug::kTileSumStride * ug::kTileCopies;   // per scan tile
+constexpr size_t kOffCounts = kOffTiles + up(kTileBytes * kNoAllocTiles);
+constexpr size_t kOffKey = kOffCounts + up(4ull * kNoAllocMaxBoxes);
 constexpr size_t kOffRank = kOffKey + up(4ull * kNoAllocMaxAgents);
 constexpr size_t kOffTmp = kOffRank + up(4ull * kNoAllocMaxAgents);
 constexpr size_t kScratchBytes = kOffTmp + up(4ull * kNoAllocMaxAgents);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-std::mutex g_mu;
-void *g_addr[64] = {nullptr};
+// cuCtxGetCurrent and cuCtxGetId, fetched through the runtime so that the
+// library needs no link against the driver library.
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
 
-// Device address of the scratch array on the current device (looked up once).
+std::mutex g_mu;
+struct CachedAddress {
+    unsigned long long ctx_id;   // 0: empty
+    void *addr;
+};
+CachedAddress g_cache[64] = {};   // one entry per device ordinal
+
+// Unique id of the context current on this thread (0 if it cannot be had).
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        cudaDriverEntryPointQueryResult q1, q2;
+        void *f1 = nullptr, *f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) ==
+                cudaSuccess && q1 == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) ==
+                cudaSuccess && q2 == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f2);
+        looked_up = true;
+    }
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return 0;
+    if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of the scratch array in the current context (looked up once
+// per context).
 int scratch_address(void **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return UG_ECUDA;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (g_addr[dev] == nullptr) {
+    unsigned long long id = current_context_id();
+    if (id == 0) {
+        // no context current yet on this thread: make the device's primary
+        // context current (cudaSetDevice initialises it), then ask again
+        if (cudaSetDevice(dev) != cudaSuccess) return UG_ECUDA;
+        id = current_context_id();
+        if (id == 0) return UG_ECUDA;
+    }
+    CachedAddress &c = g_cache[dev];
+    if (c.ctx_id != id || c.addr == nullptr) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr)
             return UG_ECUDA;
-        g_addr[dev] = p;
+        c.ctx_id = id;
+        c.addr = p;
     }
-    *out = g_addr[dev];
+    *out = c.addr;
     return UG_OK;
 }
 
@@ -67,12 +118,13 @@ extern "C" int ug_grid_build_noalloc(const float *state_in, const uint32_t *perm
                                      uint32_t max_boxes, ug_grid_info *info, int32_t *status,
                                      void *stream) {
     if (n == 0) return UG_OK;
-    if (n > kNoAllocMaxAgents || max_boxes > kNoAllocMaxBoxes) return UG_EWORKSPACE;
+    // the same argument checks as ug_grid_build, then the scratch limits
     auto al = [](const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; };
-    if (!state_in || !al(state_in, 16) || !state_sorted || !al(state_sorted, 16) || !perm_sorted ||
-        !box_start || !al(box_start, 16) || !info || !status || max_boxes < 27 ||
-        !(contact_margin >= 0.0f))
+    if (n > kMaxAgents || !state_in || !al(state_in, 16) || !state_sorted || !al(state_sorted, 16) ||
+        !perm_sorted || !box_start || !al(box_start, 16) || !info || !status || max_boxes < 27 ||
+        max_boxes > 0x7fffff00u || !(contact_margin >= 0.0f))
         return UG_EINVAL;
+    if (n > kNoAllocMaxAgents || max_boxes > kNoAllocMaxBoxes) return UG_EWORKSPACE;
     void *base = nullptr;
     const int rc = scratch_address(&base);
     if (rc != UG_OK) return rc;
@@ -89,8 +141,10 @@ extern "C" int ug_grid_build_noalloc(const float *state_in, const uint32_t *perm
     w.bytes = kScratchBytes;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // tile sums and counts must start at zero; the previous call left them zero
-    // unless it failed part-way, so clear them with the control words and bounds
-    if (cudaMemsetAsync(b, 0, kOffBounds + 4ull * kBoundsWords * kBoundsCopiesSingle, s) != cudaSuccess)
+    // unless it failed part-way, so clear them (as far as this call uses them)
+    // with the control words and the bounds
+    if (cudaMemsetAsync(b, 0, kOffTiles + kTileBytes * w.ntiles, s) != cudaSuccess ||
+        cudaMemsetAsync(b + kOffCounts, 0, 4ull * max_boxes, s) != cudaSuccess)
         return UG_ECUDA;
     SimArgs sa{};
     sa.nsims = 1;
