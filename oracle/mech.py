@@ -38,8 +38,13 @@ Simulations", Sec. III, Eq. 1 and the paragraph after it; Sec. IV-A for the grid
           pair stays within adjacent boxes, which is what Sec. IV-A relies on;
       o = min_i p_i - e  (per axis);
       b = max(floor((p - o) / e), 1);  dims = max(floor((max_i p_i - o) / e), 1) + 2;
-      key = (b_z * dims_y + b_y) * dims_x + b_x;  boxes listed in key order,
-      agents within a box in input order (stable).
+      key = (b_z * dims_y + b_y) * dims_x + b_x;  boxes listed in key order.
+  Within a box the paper fixes no order (Sec. IV-D sorts for locality); the
+  library's reading, restated here: the box edge is cut into K = 2^ks slices
+  along x, ks the largest of 0..3 with 4 * K * nboxes <= 5 * n, and agents are
+  ordered by their slice sx = floor((t_x - b_x) * K) (clamped to [0, K)), with
+  t = (p - o) / e the float32 position in box units, then by input index
+  (stable).
 
 All floating-point inputs, including parameters, are the float32 values the GPU
 sees, widened exactly to float64.
@@ -74,12 +79,23 @@ class Params:
 
 
 # --------------------------------------------------------------------- grid (FP32)
+def sub_bin_shift(n_agents: int, nboxes: int) -> int:
+    """log2 of the x slices per box: the largest ks in 0..3 with
+    4 * 2^ks * nboxes <= 5 * n_agents (0 for an empty grid)."""
+    ks = 0
+    while nboxes > 0 and ks < 3 and 4 * (nboxes << (ks + 1)) <= 5 * n_agents:
+        ks += 1
+    return ks
+
+
 def grid(state32: np.ndarray, contact_margin: float = 0.0) -> dict:
     """Uniform grid of Sec. IV-A, box edge = largest diameter (+2 margin).
 
     Returns origin, edge, dims, per-agent box coords and key, box counts and the
-    exclusive start table (length nboxes + 1), and the stable sorting
-    permutation (sorted slot -> input index)."""
+    exclusive start table (length nboxes + 1), the x slices per box (ks, and
+    each agent's slice sx), the table of slice starts (length K nboxes + 1,
+    slice sx of box k at entry k K + sx), and the sorting permutation (sorted
+    slot -> input index: by box, then slice, then input index)."""
     st = np.ascontiguousarray(state32, dtype=F32)
     p = st[:, :3]
     m2 = F32(2.0) * F32(contact_margin)
@@ -89,7 +105,8 @@ def grid(state32: np.ndarray, contact_margin: float = 0.0) -> dict:
     C = max(S, np.abs(lo).max(), np.abs(hi).max())
     e = F32(S + F32(8.0) * (np.nextafter(C, F32(np.inf)) - C))
     o = (lo - e).astype(F32)
-    b = np.floor((p - o) / e).astype(np.int64)
+    t = ((p - o) / e).astype(F32)                 # position in box units, float32
+    b = np.floor(t).astype(np.int64)
     b = np.maximum(b, 1)
     dims = np.maximum(np.floor((hi - o) / e).astype(np.int64), 1) + 2
     key = (b[:, 2] * dims[1] + b[:, 1]) * dims[0] + b[:, 0]
@@ -97,9 +114,16 @@ def grid(state32: np.ndarray, contact_margin: float = 0.0) -> dict:
     counts = np.bincount(key, minlength=nboxes)
     start = np.zeros(nboxes + 1, dtype=np.int64)
     start[1:] = np.cumsum(counts)
-    perm = np.argsort(key, kind="stable")
+    ks = sub_bin_shift(len(st), nboxes)
+    K = 1 << ks
+    frac = (t[:, 0] - b[:, 0].astype(F32)).astype(F32)      # exact in float32
+    sx = np.clip(np.floor(frac * F32(K)).astype(np.int64), 0, K - 1)
+    skey = key * K + sx
+    table = np.zeros(K * nboxes + 1, dtype=np.int64)
+    table[1:] = np.cumsum(np.bincount(skey, minlength=K * nboxes))
+    perm = np.argsort(skey, kind="stable")
     return dict(origin=o, edge=F32(e), dims=dims, box=b, key=key, nboxes=nboxes,
-                counts=counts, start=start, perm=perm)
+                counts=counts, start=start, ks=ks, sub=sx, table=table, perm=perm)
 
 
 # --------------------------------------------------------------------- pairs (FP64)

@@ -9,7 +9,9 @@
   * closed-form displacements (Sec. III rules as read here: strict adherence,
     u = (dt / m) F with m = density (pi/6) d^3, the cap along u), with dt != 1
     and a capped case;
-  * a hand-worked grid (edge, padding layer, x-fastest keys, exclusive starts)
+  * a hand-worked grid (edge, padding layer, x-fastest keys, exclusive starts),
+    the x slices that order agents inside a box (the density rule's
+    thresholds, a hand-worked order) and the slice order on random populations
     and the uniform grid's completeness condition (Sec. IV-A): every contact
     pair lies in adjacent boxes;
   * the adjoint against FP64 central finite differences of the forward, on
@@ -171,7 +173,65 @@ def check_grid_hand():
                 and list(g["start"][20:25]) == [0, 0, 1, 1, 2] and g["start"][-1] == 2)
 
 
+def check_grid_slices_hand():
+    """The order inside a box (the library's reading; the paper fixes none).
+    44 spheres of d = 10 in one box, x cycling through 9, 1, 7, 3: the grid is
+    3x3x3 = 27 boxes, so 4 * 2 * 27 = 216 <= 5 * 44 = 220 gives K = 2 slices
+    (K = 4 would need 432 <= 220).  With o = 1 - e, t_x = 1 + (x - 1) / e puts
+    x = 1, 3 in slice 0 and x = 7, 9 in slice 1 (fractions 0, 0.2, 0.6, 0.8), so
+    the sorted order is every x = 1 or 3 agent (the odd input indices) in input
+    order, then the x = 7 or 9 ones (the even indices); 43 agents give K = 1
+    and plain input order."""
+    x = np.array([[9, 0, 0, 10], [1, 0, 0, 10], [7, 0, 0, 10], [3, 0, 0, 10]] * 11, np.float32)
+    g = O.grid(x)
+    ok = g["ks"] == 1 and g["nboxes"] == 27 and list(g["sub"][:4]) == [1, 0, 1, 0]
+    ok &= list(g["perm"]) == list(range(1, 44, 2)) + list(range(0, 44, 2))
+    # the slice table: box 13 (the middle one) holds 22 + 22 agents
+    ok &= list(g["table"][26:29]) == [0, 22, 44] and g["table"][-1] == 44
+    g43 = O.grid(x[:43])
+    ok &= g43["ks"] == 0 and list(g43["perm"]) == list(range(43))
+    return bool(ok)
+
+
+def check_grid_slice_order(state32, margin=0.0):
+    """Sorted agents of every box come by slice, then by input index, and the
+    slice table counts them."""
+    g = O.grid(state32, margin)
+    K = 1 << g["ks"]
+    perm = g["perm"]
+    sk = g["key"][perm] * K + g["sub"][perm]
+    ok = bool(np.all(np.diff(sk) >= 0))
+    same = np.diff(sk) == 0
+    ok &= bool(np.all(np.diff(perm)[same] > 0))
+    # a slice spans 1/K of its box along x
+    o, e = g["origin"].astype(np.float64), float(g["edge"])
+    fx = (state32[:, 0].astype(np.float64) - o[0]) / e - g["box"][:, 0]
+    ok &= bool(np.all(fx >= g["sub"] / K - 1e-5)) and bool(np.all(fx < (g["sub"] + 1) / K + 1e-5))
+    ok &= bool(np.array_equal(np.diff(g["table"]), np.bincount(g["key"] * K + g["sub"],
+                                                              minlength=K * g["nboxes"])))
+    return ok
+
+
 # ------------------------------------------------------------------ tests
+def test_sub_bin_rule_values():
+    """4 * 2^ks * nboxes <= 5 * n, ks <= 3: thresholds worked by hand for 27 boxes."""
+    assert [O.sub_bin_shift(n, 27) for n in (0, 43, 44, 86, 87, 172, 173, 10 ** 6)] == \
+        [0, 0, 1, 1, 2, 2, 3, 3]
+    assert O.sub_bin_shift(10, 0) == 0
+
+
+def test_grid_slices_hand_example():
+    assert check_grid_slices_hand()
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_grid_slice_order(seed):
+    assert check_grid_slice_order(P.small_uniform(seed))
+    assert check_grid_slice_order(P.uniform_cube(3000, 60.0, 8.0, 12.0, seed))        # K = 4
+    assert check_grid_slice_order(P.jittered_lattice(4096, 16, 9.0, 1.5, 9.0, 11.0, seed), 1.5)
+    assert O.grid(P.uniform_cube(3000, 60.0, 8.0, 12.0, seed))["ks"] >= 2
+
+
 def test_worked_examples():
     assert check_worked_examples() < 1e-12
 
@@ -462,8 +522,18 @@ def _plant(monkeypatch, which):
                 start[-1] = start[-2]
             else:
                 start[1:] = np.cumsum(counts)
+            ks, sub = g["ks"], g["sub"]
+            if which == "grid_slices_doubled":      # one more slice level than the rule gives
+                ks = ks + 1
+                sub = np.minimum(np.floor(((state32[:, 0] - g["origin"][0]) / g["edge"]).astype(np.float32)
+                                          - b[:, 0]) * (1 << ks), (1 << ks) - 1).astype(np.int64)
+            K = 1 << ks
+            skey = key * K + sub
+            perm = np.argsort(key if which == "grid_box_input_order" else skey, kind="stable")
+            table = np.zeros(K * nboxes + 1, dtype=np.int64)
+            table[1:] = np.cumsum(np.bincount(skey, minlength=K * nboxes))
             g.update(box=b, dims=dims, key=key, nboxes=nboxes, counts=counts, start=start,
-                     perm=np.argsort(key, kind="stable"))
+                     ks=ks, sub=sub, table=table, perm=perm)
             return g
         monkeypatch.setattr(M, "grid", grid)
         monkeypatch.setattr(O, "grid", grid)
@@ -475,13 +545,15 @@ def _pins_pass(which):
     n_ok = check_newton3(P.small_uniform(0)[:1500]) < 1e-13
     d_ok = check_displacement_hand() == 0.0
     b_ok = check_grid_hand() and check_grid_completeness(P.small_uniform(0))
+    b_ok = b_ok and check_grid_slices_hand()
     return g_ok and p_ok and n_ok and d_ok and b_ok
 
 
 @pytest.mark.parametrize("which", ["drop_gamma", "wrong_sign", "diameter_as_radius", "R_sum",
                                    "transposed_index", "adherence_ge", "mass_from_radius",
                                    "dt_ignored", "cap_ignored", "grid_no_padding",
-                                   "grid_key_y_fastest", "grid_inclusive_scan"])
+                                   "grid_key_y_fastest", "grid_inclusive_scan",
+                                   "grid_box_input_order", "grid_slices_doubled"])
 def test_planted_mistakes_are_caught(monkeypatch, which):
     assert _pins_pass("none")
     _plant(monkeypatch, which)
