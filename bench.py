@@ -1,20 +1,22 @@
 #!/usr/bin/env python
 """Throughput of the mechanical-interaction step (agent-steps/s).
 
-Workload: 2^20 cells on a jittered 102^3 lattice (spacing 9, jitter +-1.5,
-diameters U[9, 11]), 100 fused steps with the grid rebuilt every step.  One
-bench step = those 100 steps from the same initial rows, so a bench step
-processes 2^20 * 100 agent-steps.  Before each timed step a 256 MB buffer is
-written to flush the 129 MB L2 (outside the step's CUDA events).
+Workload (the paper's benchmark B at GB300 size): 4,194,304 cells with centres
+uniform in a cube sized for a mean of 8 overlapping neighbours, diameters
+U[8, 12], maximum displacement 0 (benchmark B's rule), 20 fused steps with the
+grid rebuilt every step.  One bench step = those 20 steps, so it processes
+4,194,304 * 20 agent-steps.  Before each timed step a 256 MB buffer is written
+to flush the 129 MB L2 (outside the step's CUDA events).
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 oracle on the
-host cores on a bounded sample of the same workload instead.
+host cores instead (a bounded sample of the same workload per bench step).
 
 Multi-GPU: the path is weak-scaled as independent replicas (each rank runs its
 own population; no collective on the data path); the barrier and the max over
 ranks only frame the timing.
 """
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -28,67 +30,75 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-N_LATTICE = 1 << 20
-SIM_STEPS = 100
+N_AGENTS = 1 << 22
+MEAN_NEIGHBOURS = 8.0
+POP_SEED = 8                        # rank r uses POP_SEED + 1000 r
+SIM_STEPS = 20
+WORKLOAD = ("density cube: 4,194,304 cells, centres uniform in a cube sized for a mean of 8 "
+            "overlapping neighbours, d U[8,12], max displacement 0; 20 fused steps (grid rebuilt "
+            "every step) per bench step")
 BYTES_PER_AGENT_SWEEP = 32          # sweep + move: read 16 B row, write 16 B row
 BYTES_PER_AGENT_STEP = 88           # whole step (grid bin 16, scatter 40, sweep 32)
 BYTES_PER_BOX = 12
-# algorithmic FP32 operations: distance pre-test per candidate pair (3 sub,
-# 3 mul/fma, 1 add, 1 mul, 1 compare), Eq. 1 per contact (delta: sqrt + sub; R:
-# mul, add, div; sqrt(R delta): mul + sqrt; phi: 2 mul + sub; direction: div +
-# 3 mul; sum: 3 add) and the displacement per agent (|F|, mass, dt/m, 3 mul,
-# |v|, cap test, 3 add)
+# algorithmic FP32 operations of the method: distance pre-test per candidate in
+# the 27 surrounding boxes (3 sub, 3 mul/fma, 1 add, 1 mul, 1 compare), Eq. 1 per
+# contact (delta: sqrt + sub; R: mul, add, div; sqrt(R delta): mul + sqrt; phi:
+# 2 mul + sub; direction: div + 3 mul; sum: 3 add) and the displacement per
+# agent (|F|, mass, dt/m, 3 mul, |v|, cap test, 3 add)
 FLOPS_PER_CANDIDATE = 9
 FLOPS_PER_CONTACT = 17
 FLOPS_PER_AGENT = 25
-# FP32 roof: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
+# FP32 roof (derived: MEASURED_PEAKS.json has no FP32 figure): 152 SMs x 128
+# FP32 lanes x 2 flop (FMA) x 2.07 GHz; issue roof: 4 schedulers per SM, one
+# warp instruction each per clock
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# DRAM bytes (read + write) of one k_sweep2 launch on this workload, from the
-# ncu capture summarised in profiles/k_sweep2_lattice1m.md (cache flushed)
-SWEEP_DRAM_BYTES = 23.521792e6 + 0.320256e6
-SWEEP_DRAM_BYTES_SRC = "9b362eb61c0f7119"      # sha256[:16] of ug_sweep2.cu + ug_internal.cuh when captured
-
-
-# Warp instructions of one k_sweep2 launch on this workload, from the same ncu
-# capture (and valid under the same source check) as the DRAM bytes above, and
-# the SMs' issue limit: one warp instruction per scheduler per clock, four
-# schedulers per SM.
-SWEEP_WARP_INST = 89_700_118
 ISSUE_PEAK_GINST_S = 152 * 4 * 2.07
+# One launch of the sweep on this workload under ncu (cache flushed): DRAM bytes
+# read + written and warp instructions executed.  They describe the sweep's
+# source as it was captured (sha256[:16] of the files below) and are reported
+# as null once that source changes.
+SWEEP_SOURCES = ("ug_sweep2.cu", "ug_internal.cuh")
+SWEEP_CAPTURE = {"src": None, "dram_bytes": None, "warp_inst": None}
+
+
+def sweep_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, "paper_2105_00039_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def sweep_capture():
+    """The captured counters if the sweep's source is unchanged since, else None."""
+    if SWEEP_CAPTURE["src"] is None or SWEEP_CAPTURE["src"] != sweep_source_hash():
+        return None
+    return SWEEP_CAPTURE
 
 
 def issue_roofline(avg_launch_ms: float):
-    """The sweep against the instruction-issue limit (the bound that holds it),
-    or None once its source has changed since the instruction count was taken."""
-    if sweep_traffic() is None:
+    """The sweep against the instruction-issue limit, or None without a current
+    capture of its instruction count."""
+    cap = sweep_capture()
+    if cap is None:
         return None
-    achieved = SWEEP_WARP_INST / (avg_launch_ms / 1000.0) / 1e9
-    return {"warp_inst_per_launch": SWEEP_WARP_INST, "achieved_ginst_s": achieved,
+    achieved = cap["warp_inst"] / (avg_launch_ms / 1000.0) / 1e9
+    return {"warp_inst_per_launch": cap["warp_inst"], "achieved_ginst_s": achieved,
             "peak_ginst_s": ISSUE_PEAK_GINST_S, "frac": achieved / ISSUE_PEAK_GINST_S,
             "peak_source": "derived: 152 SMs x 4 schedulers x 1 warp instruction per clock "
                            "x 2.07 GHz; instructions per launch from ncu"}
-
-
-def sweep_traffic():
-    """The captured DRAM bytes if the sweep's source is unchanged since, else None."""
-    import hashlib
-    h = hashlib.sha256()
-    for f in ("ug_sweep2.cu", "ug_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2105_00039_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return SWEEP_DRAM_BYTES if h.hexdigest()[:16] == SWEEP_DRAM_BYTES_SRC else None
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the batched, adjoint and density-sweep rows")
+                    help="skip the density, batched, adjoint and comparison rows")
     return ap.parse_args()
 
 
@@ -171,23 +181,108 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_rate(state, nsteps_sample: int):
-    """The FP64 oracle as it stands, one full step of the whole population per
-    sample step; returns (agent-steps/s, seconds)."""
+# ---------------------------------------------------------------------------- CPU oracle
+def _oracle_chunk(args):
+    """One process's share of a sampled oracle step: the population is rebuilt
+    from its seed, the oracle's sampled step (its own kd-tree over all cells,
+    then the listed cells against every cell) is timed."""
+    n, nbar, seed, lo, hi, stride = args
     import oracle as O
+    from paper_2105_00039_gb300 import populations as P
+    st = P.density_cube(n, nbar, seed=seed)
+    idx = np.arange(lo, hi, stride, dtype=np.int64)
     t0 = time.perf_counter()
-    st = state
-    for _ in range(nsteps_sample):
-        st = O.step(st, O.Params())["state"]
-    dt = time.perf_counter() - t0
-    return len(state) * nsteps_sample / dt, dt
+    O.step_sampled(st, idx, O.Params(max_disp=0.0))
+    return len(idx), time.perf_counter() - t0
 
 
+class OraclePool:
+    """The FP64 oracle on the host's cores: `procs` spawned processes (spawn, so
+    that no CUDA state is inherited), each running the oracle as it stands on
+    its own slice of the cells."""
+
+    def __init__(self, procs: int):
+        import multiprocessing as mp
+        self.procs = procs
+        self.pool = mp.get_context("spawn").Pool(procs) if procs > 1 else None
+
+    def step(self, n, nbar, seed, fraction=1.0):
+        """One sampled step over `fraction` of the cells (every cell when 1):
+        returns (cells evaluated, wall seconds of the slowest process)."""
+        stride = max(1, int(round(1.0 / fraction)))
+        per = (n + self.procs - 1) // self.procs
+        jobs = [(n, nbar, seed, p * per, min(n, (p + 1) * per), stride) for p in range(self.procs)]
+        res = self.pool.map(_oracle_chunk, jobs) if self.pool else [_oracle_chunk(jobs[0])]
+        return sum(r[0] for r in res), max(r[1] for r in res)
+
+    def close(self):
+        if self.pool:
+            self.pool.close()
+            self.pool.join()
+
+
+def cpu_oracle_baseline():
+    """The oracle on all host cores (one full step of every cell, split over
+    the cores) and on one core (a sample of the cells, its kd-tree included)."""
+    cores = os.cpu_count() or 1
+    pool = OraclePool(cores)
+    try:
+        cells, secs = pool.step(N_AGENTS, MEAN_NEIGHBOURS, POP_SEED)
+    finally:
+        pool.close()
+    one = OraclePool(1)
+    cells1, secs1 = one.step(N_AGENTS, MEAN_NEIGHBOURS, POP_SEED, fraction=1.0 / 8.0)
+    pinning = "none (the OS scheduler places the processes)"
+    return {"value": cells / secs, "unit": "agent-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"one FP64 oracle step of all {cells} cells of the bench workload, split over "
+                      f"{cores} spawned processes (each builds its own kd-tree over all cells); "
+                      f"slowest process {secs:.1f} s",
+            "pinning": pinning,
+            "one_core": {"value": cells1 / secs1, "unit": "agent-steps/s", "cores": 1,
+                         "sample": f"every 8th cell ({cells1} cells) against all cells, kd-tree "
+                                   f"included, {secs1:.1f} s"}}
+
+
+def run_reference(args, world, rank, pg):
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    pool = OraclePool(cores)
+    frac = 0.5
+    try:
+        for _ in range(args.warmup):
+            pool.step(N_AGENTS, MEAN_NEIGHBOURS, POP_SEED, frac)
+        cells, total = 0, 0.0
+        for _ in range(args.steps):
+            c, dt = pool.step(N_AGENTS, MEAN_NEIGHBOURS, POP_SEED, frac)
+            cells += c
+            total += dt
+    finally:
+        pool.close()
+    value = cells / total if total > 0 else 0.0
+    line = {
+        "impl": "reference", "metric": "agent-steps/s", "value": value, "unit": "agent-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * total / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_agents": N_AGENTS,
+                   "sample": "every 2nd cell against all cells per bench step (one oracle step)",
+                   "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "agent-steps/s", "cores": cores, "kind": "oracle",
+                         "sample": f"every 2nd cell of the 4,194,304 against all cells per bench step, "
+                                   f"split over {cores} spawned processes, kd-tree built in each"},
+        "e2e": {"value": value, "unit": "agent-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------- measurement
 def candidates_and_contacts(U, x, prm):
-    """Mean candidates (agents in the 27 surrounding boxes, self excluded) and
-    contacts per agent of a population, from the library's grid and forces.
-    Measurement only: the box counts are summed over 3x3x3 neighbourhoods with
-    torch on the box table."""
+    """Mean candidates (agents in the 27 surrounding boxes, self excluded),
+    contacts per agent and the number of boxes of a population, from the
+    library's grid and forces.  Measurement only: the box counts are summed
+    over 3x3x3 neighbourhoods with torch on the per-box table."""
     import torch
     srt, perm, start, info, _ = U.grid_build(x, contact_margin=prm.contact_margin)
     g = U.grid_info_from_bytes(info)
@@ -198,36 +293,118 @@ def candidates_and_contacts(U, x, prm):
     n = x.shape[0]
     cand = float((cnt * nb).sum().item() - n) / n
     F = U.compute_forces(srt, start, info, prm)
-    return cand, float(F[:, 3].double().mean().item())
+    return cand, float(F[:, 3].double().mean().item()), int(g["nboxes"])
 
 
-def run_reference(args, world, rank, pg):
+def _timed(fn, reps, flush=None):
+    """Mean milliseconds of fn() over reps runs, CUDA events on the current
+    stream, L2 flushed before each run (outside the events)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    tot = 0.0
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    return tot / reps
+
+
+class Population:
+    """One population on the device with a Stepper sized for it, and the
+    three ways of stepping it the rows below compare."""
+
+    def __init__(self, U, st, prm, dev, slack=1.05):
+        import torch
+        self.U, self.prm = U, prm
+        self.n = len(st)
+        self.x0 = torch.from_numpy(st).to(dev)
+        self.mb = U.estimate_max_boxes(self.x0, prm.contact_margin, slack=slack)
+        self.sp = U.Stepper(self.n, self.mb, dev)
+        self.x = torch.empty_like(self.x0)
+        self.perm = torch.empty(self.n, dtype=torch.int32, device=dev)
+        self.lib = U.load()
+        self.one = torch.tensor([0, self.n], dtype=torch.int32, device=dev)
+        self.pdev = prm.as_tensor(dev)[None]
+        self.walks = {}
+        for name, walk in (("full_runs", 1), ("windows_always", 2)):
+            t = U.ug_tuning()
+            t.agents_per_lane, t.sweep_block, t.neighbour_walk = 2, 128, walk
+            self.walks[name] = t
+
+    def reset(self):
+        self.x.copy_(self.x0)
+        self.U._check(self.lib.ug_iota(self.U._ptr(self.perm), self.n, self.U._stream()), "ug_iota")
+
+    def run(self, nsteps, how="default"):
+        """ug_step ("default": neighbour-row windows where they pay), every pair
+        once, or one simulation through ug_step_batched walking the full runs
+        or the windows at every grid density."""
+        self.reset()
+        if how == "default":
+            self.sp.step(self.x, self.perm, self.prm, nsteps)
+        elif how == "pairs_once":
+            self.sp.step(self.x, self.perm, self.prm, nsteps, pairs_once=True)
+        else:
+            self.sp.step_batched(self.x, self.perm, self.one, self.pdev, nsteps, self.walks[how])
+
+    def traced(self, nsteps, events):
+        self.reset()
+        self.sp.step_traced(self.x, self.perm, self.prm, nsteps, events)
+
+
+def kernel_split(pop, nsteps, reps=1):
+    """Per-kernel device time per step (us), from ug_step_traced (events
+    between the kernels, which also un-chains them)."""
+    import torch
+    names = ("key", "scan", "place", "canon", "sweep")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 + 5 * nsteps)]
+    for e in ev:
+        e.record()
+    split = {nm: 0.0 for nm in ("bounds",) + names}
+    for _ in range(reps):
+        pop.traced(nsteps, ev)
+        ev[-1].synchronize()
+        split["bounds"] += ev[0].elapsed_time(ev[1])
+        for t in range(nsteps):
+            for j, nm in enumerate(names):
+                split[nm] += ev[1 + 5 * t + j].elapsed_time(ev[2 + 5 * t + j])
+    pop.sp.check("traced")
+    return {k: 1000.0 * v / (reps * (1 if k == "bounds" else nsteps)) for k, v in split.items()}
+
+
+def density_row(U, dev, flush, hbm, n, nbar, nsteps=SIM_STEPS, reps=2, seed=None):
+    """One Benchmark-B style population: agent-steps/s with ug_step, with the
+    full three-box runs, with the windows at any density, and with every pair
+    once; the kernel split, and the step's and the sweep's rooflines."""
     from paper_2105_00039_gb300 import populations as P
-    if rank != 0:
-        return
-    st = P.lattice_1m(0)
-    for _ in range(args.warmup):
-        cpu_oracle_rate(st, 1)
-    times = []
-    for _ in range(args.steps):
-        _, dt = cpu_oracle_rate(st, 1)
-        times.append(dt)
-    total = sum(times)
-    value = len(st) * args.steps / total
-    line = {
-        "impl": "reference", "metric": "agent-steps/s", "value": value, "unit": "agent-steps/s",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "lattice_1m: 2^20 cells, 102^3 lattice spacing 9 jitter 1.5, d U[9,11]",
-                   "n_agents": len(st), "sample": "1 oracle step of the full population per bench step",
-                   "l2": "n/a (CPU)"},
-        "cpu_baseline": {"value": value, "unit": "agent-steps/s", "cores": 1, "kind": "oracle",
-                         "sample": "1 FP64 oracle step (cKDTree pair search + numpy Eq. 1) of all 2^20 cells per bench step"},
-        "e2e": {"value": value, "unit": "agent-steps/s", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
+    prm = U.Params(max_disp=0.0)
+    pop = Population(U, P.density_cube(n, float(nbar), seed=nbar if seed is None else seed), prm, dev)
+    out = {"n_agents": n, "mean_neighbours_target": nbar}
+    for how in ("default", "full_runs", "windows_always", "pairs_once"):
+        pop.run(nsteps, how)
+        pop.sp.check(how)
+        ms = _timed(lambda: pop.run(nsteps, how), reps, flush)
+        pop.sp.check(how)
+        out[how] = {"agent_steps_per_s": n * nsteps / (ms / 1e3), "ms_per_step": ms / nsteps}
+    split = kernel_split(pop, nsteps)
+    cand, cont, boxes = candidates_and_contacts(U, pop.x0, prm)
+    per_step_s = out["default"]["ms_per_step"] / 1e3
+    alg = BYTES_PER_AGENT_STEP * n + BYTES_PER_BOX * boxes
+    flops = n * (FLOPS_PER_CANDIDATE * cand + FLOPS_PER_CONTACT * cont + FLOPS_PER_AGENT)
+    tflops = flops / (split["sweep"] * 1e-6) / 1e12
+    out.update({"step_alg_gbs": alg / per_step_s / 1e9, "step_hbm_frac": alg / per_step_s / 1e9 / hbm,
+                "boxes": boxes, "candidates_per_agent": cand, "contacts_per_agent": cont,
+                "sweep_alu_tflops": tflops, "sweep_alu_frac": tflops / FP32_PEAK_TFLOPS,
+                "windows_speedup_over_full_runs": out["full_runs"]["ms_per_step"] /
+                                                  out["windows_always"]["ms_per_step"],
+                "kernel_us_per_step_traced": split})
+    return out
 
 
 def run_ours(args, world, rank, local, pg):
@@ -238,125 +415,91 @@ def run_ours(args, world, rank, local, pg):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    st = P.lattice_1m(seed=rank)
+    st = P.density_cube(N_AGENTS, MEAN_NEIGHBOURS, seed=POP_SEED + 1000 * rank)
     n = len(st)
-    prm = U.Params()
-    x0 = torch.from_numpy(st).to(dev)
-    x = torch.empty_like(x0)
-    max_boxes = U.estimate_max_boxes(x0, prm.contact_margin, slack=1.5)
-    sp = U.Stepper(n, max_boxes, dev)
-    perm = torch.empty(n, dtype=torch.int32, device=dev)
-    nev = 2 + 5 * SIM_STEPS
+    prm = U.Params(max_disp=0.0)
+    pop = Population(U, st, prm, dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    lib = U.load()
     stream = torch.cuda.current_stream()
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        hbm = float(json.load(f)["hbm_gbs"])
 
-    def reset():
-        x.copy_(x0)
-        U._check(lib.ug_iota(U._ptr(perm), n, U._stream()), "ug_iota")
-
-    # warm-up (also creates the CUDA handles of the trace events)
-    events = [torch.cuda.Event(enable_timing=True) for _ in range(nev)]
-    for e in events:
-        e.record(stream)
     for _ in range(args.warmup):
-        reset()
-        sp.step(x, perm, prm, SIM_STEPS)
-    sp.check("warm-up")
+        pop.run(SIM_STEPS)
+    pop.sp.check("warm-up")
     torch.cuda.synchronize()
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    kern_ms = {k: 0.0 for k in ("bounds", "key", "scan", "place", "canon", "sweep")}
-    names = ["key", "scan", "place", "canon", "sweep"]
     if pg is not None:
         pg.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        # the metric: K plain bench steps (kernels chained with programmatic
-        # dependent launch), each preceded by an L2 flush outside its events
+        # the metric: K bench steps (kernels chained with programmatic dependent
+        # launch), each preceded by an L2 flush outside its events
         wall0 = time.perf_counter()
         for k in range(args.steps):
             flush.zero_()
             starts[k].record(stream)
-            reset()
-            sp.step(x, perm, prm, SIM_STEPS)
+            pop.run(SIM_STEPS)
             ends[k].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
-        # per-kernel durations: the same K bench steps again with CUDA events
-        # recorded between the kernels (which also un-chains them)
-        for k in range(args.steps):
-            flush.zero_()
-            reset()
-            sp.step_traced(x, perm, prm, SIM_STEPS, events)
-            events[-1].synchronize()
-            kern_ms["bounds"] += events[0].elapsed_time(events[1])
-            for t in range(SIM_STEPS):
-                for j, nm in enumerate(names):
-                    kern_ms[nm] += events[1 + 5 * t + j].elapsed_time(events[2 + 5 * t + j])
+        # per-kernel durations: the same bench steps with events between kernels
+        split = kernel_split(pop, SIM_STEPS, reps=args.steps)
         torch.cuda.synchronize()
     if pg is not None:
         pg.barrier()
-    sp.check("timed steps")
+    pop.sp.check("timed steps")
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     tot_ms = reduce_max(pg, sum(step_ms), dev)
     ms_per_step = tot_ms / args.steps
     value = world * n * SIM_STEPS * args.steps / (tot_ms / 1000.0)
 
-    # roofline of the dominant kernel (time-weighted, per launch)
-    launches = {"bounds": args.steps, **{nm: args.steps * SIM_STEPS for nm in names}}
-    dom = max(kern_ms, key=kern_ms.get)
-    avg_launch_ms = kern_ms[dom] / launches[dom]
-    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-        peaks = json.load(f)
-    hbm = float(peaks["hbm_gbs"])
-    alg_bytes = {"sweep": BYTES_PER_AGENT_SWEEP * n, "canon": 48 * n, "key": 24 * n,
-                 "place": 16 * n, "scan": 12 * max_boxes, "bounds": 16 * n}[dom]
-    achieved = alg_bytes / (avg_launch_ms / 1000.0) / 1e9
-    # candidates and contacts at the start and the end of a bench step
-    c0, k0 = candidates_and_contacts(U, x0, prm)
-    c1, k1 = candidates_and_contacts(U, x.contiguous(), prm)
-    cand, cont = 0.5 * (c0 + c1), 0.5 * (k0 + k1)
+    # roofline of the dominant kernel (the sweep), per launch, and of the step
+    avg_launch_ms = split["sweep"] / 1000.0
+    cand, cont, boxes = candidates_and_contacts(U, pop.x0, prm)   # frozen population
     alg_flops = n * (FLOPS_PER_CANDIDATE * cand + FLOPS_PER_CONTACT * cont + FLOPS_PER_AGENT)
     alu_tflops = alg_flops / (avg_launch_ms / 1000.0) / 1e12
-    # whole-step HBM roofline (algorithmic bytes of the method per step)
-    step_alg = (BYTES_PER_AGENT_STEP * n + BYTES_PER_BOX * max_boxes / 1.5) * SIM_STEPS
-    step_gbs = step_alg / (ms_per_step / 1000.0) / 1e9
+    sweep_bytes = BYTES_PER_AGENT_SWEEP * n
+    step_alg = BYTES_PER_AGENT_STEP * n + BYTES_PER_BOX * boxes
+    step_gbs = step_alg / (ms_per_step / SIM_STEPS / 1000.0) / 1e9
+    cap = sweep_capture()
 
     line = {
         "metric": "agent-steps/s", "value": value, "unit": "agent-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "lattice_1m: 2^20 cells, 102^3 lattice spacing 9 jitter 1.5, d U[9,11]; "
-                               "100 fused steps (grid rebuilt each step) per bench step",
-                   "n_agents": n, "sim_steps_per_step": SIM_STEPS, "max_boxes": max_boxes,
+        "config": {"workload": WORKLOAD, "n_agents": n, "mean_neighbours": MEAN_NEIGHBOURS,
+                   "sim_steps_per_step": SIM_STEPS, "boxes": boxes, "max_boxes": pop.mb,
                    "l2": "flushed (256 MB write) before each timed step, outside its events",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": alu_tflops,
+        "roofline": {"bound": "alu", "kernel": "sweep", "achieved": alu_tflops,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": alu_tflops / FP32_PEAK_TFLOPS,
-                     "traffic": sweep_traffic() if dom == "sweep" else None,
+                     "traffic": cap["dram_bytes"] if cap else None,
                      "avg_launch_us": avg_launch_ms * 1000.0,
                      "alg_flops_per_launch": alg_flops,
                      "candidates_per_agent": cand, "contacts_per_agent": cont,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                     "note": "instruction issue: 68% of issue slots busy, 89.7M warp instructions per launch (ncu), see profiles/k_sweep2_lattice1m.md",
-                     "issue": issue_roofline(avg_launch_ms) if dom == "sweep" else None,
-                     "hbm": {"achieved_gbs": achieved, "peak_gbs": hbm, "frac": achieved / hbm,
-                             "alg_bytes_per_launch": alg_bytes,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz "
+                                    "(MEASURED_PEAKS.json has no FP32 figure)",
+                     "issue": issue_roofline(avg_launch_ms),
+                     "hbm": {"achieved_gbs": sweep_bytes / (avg_launch_ms / 1000.0) / 1e9,
+                             "peak_gbs": hbm, "alg_bytes_per_launch": sweep_bytes,
+                             "frac": sweep_bytes / (avg_launch_ms / 1000.0) / 1e9 / hbm,
                              "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
-                     "step_alg_gbs": step_gbs, "step_hbm_frac": step_gbs / hbm},
-        "kernel_ms_share": {k: v / sum(kern_ms.values()) for k, v in kern_ms.items()},
+                     "step_alg_bytes": step_alg, "step_alg_gbs": step_gbs,
+                     "step_hbm_frac": step_gbs / hbm},
+        "kernel_us_per_step_traced": split,
+        "kernel_share": {k: v / sum(split.values()) for k, v in split.items()},
         "gpu_launches": args.steps * (2 + 5 * SIM_STEPS),
-        "kernel_ms_per_step_traced": {k: v / (args.steps * SIM_STEPS) for k, v in kern_ms.items()},
         "clocks": clk.summary(),
         "wall_s_timed_region": wall,
     }
 
     # end to end through the public API: pinned host rows in, rows (by id) out
     if not args.no_e2e:
-        sim = U.Simulation(n, max_boxes, dev)
+        sim = U.Simulation(n, pop.mb, dev)
         host_in = torch.from_numpy(st).pin_memory()
         host_out = torch.empty((n, 4), dtype=torch.float32).pin_memory()
         for _ in range(2):
@@ -377,22 +520,30 @@ def run_ours(args, world, rank, local, pg):
         line["e2e"] = {"value": world * n * SIM_STEPS * args.steps / (e_ms / 1000.0),
                        "unit": "agent-steps/s", "h2d_bytes_per_step": 16 * n,
                        "d2h_bytes_per_step": 16 * n}
+        del sim
 
     # the extra rows and the CPU baselines are single-GPU measurements: a
     # multi-GPU run reports only the headline
     if not args.no_extras and world == 1:
+        walk = {"workload": "the headline population, the same steps",
+                "default_ms_per_step": ms_per_step / SIM_STEPS}
+        for how in ("full_runs", "windows_always"):
+            pop.run(SIM_STEPS, how)
+            pop.sp.check(how)
+            walk[how + "_ms_per_step"] = _timed(lambda: pop.run(SIM_STEPS, how), args.steps, flush) / SIM_STEPS
+        line["walk"] = walk
+        del pop
+        torch.cuda.empty_cache()
+        line["density_sweep"] = measure_density(U, dev, flush, hbm)
+        line["lattice_1m"] = measure_lattice(U, dev, flush, hbm)
         line["batched"] = measure_batched(dev, flush)
         line["adjoint"] = measure_adjoint(dev, flush)
-        line["density_sweep"] = measure_density(dev, flush)
         line["version_ladder"] = measure_ladder(dev, flush)
-        line["lattice_margin"] = measure_lattice_margin(dev, flush)
         line["pairs_once"] = measure_pairs_once(dev, flush)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, secs = cpu_oracle_rate(st, 6)
-        line["cpu_baseline"] = {"value": rate, "unit": "agent-steps/s", "cores": 1, "kind": "oracle",
-                                "sample": f"6 FP64 oracle steps of all 2^20 cells ({secs:.1f} s)"}
-        line["cpu_grid_baseline"] = cpu_grid_rate(st, 50)
+        line["cpu_baseline"] = cpu_oracle_baseline()
+        line["cpu_grid_baseline"] = cpu_grid_rate(st, 10)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -414,31 +565,52 @@ def cpu_grid_rate(st, nsteps):
 
 
 # ---------------------------------------------------------------------------- extra rows
-def _timed(fn, reps, flush=None):
-    """Mean milliseconds of fn() over reps runs, CUDA events on the current
-    stream, L2 flushed before each run (outside the events)."""
+def measure_density(U, dev, flush, hbm):
+    """Benchmark-B style density sweep: 4,194,304 cells at a mean of 2, 8, 32, 64
+    overlapping neighbours and 16,777,216 at 12 (the out-of-cache run), max
+    displacement 0, 20 steps each."""
     import torch
-    stream = torch.cuda.current_stream()
-    tot = 0.0
-    for _ in range(reps):
-        if flush is not None:
-            flush.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        fn()
-        b.record(stream)
-        b.synchronize()
-        tot += a.elapsed_time(b)
-    return tot / reps
+    rows = []
+    for n, nbar in ((1 << 22, 2), (1 << 22, 8), (1 << 22, 32), (1 << 22, 64), (1 << 24, 12)):
+        rows.append(density_row(U, dev, flush, hbm, n, nbar))
+        torch.cuda.empty_cache()
+    return rows
+
+
+def measure_lattice(U, dev, flush, hbm, nsteps=100, reps=2):
+    """2^20 cells on the jittered 102^3 lattice (spacing 9, jitter 1.5, d U[9,11]),
+    100 fused steps with the default displacement rules, without and with a
+    contact margin of 1.5 (the variant that reaches ~12 overlapping neighbours)."""
+    from paper_2105_00039_gb300 import populations as P
+    st = P.lattice_1m(0)
+    n = len(st)
+    out = {"workload": "2^20 cells, first sites of a 102^3 lattice (spacing 9, jitter 1.5, d U[9,11]), "
+                       f"{nsteps} fused steps"}
+    for name, margin in (("margin_0", 0.0), ("margin_1.5", 1.5)):
+        prm = U.Params(contact_margin=margin)
+        pop = Population(U, st, prm, dev, slack=1.2)
+        row = {}
+        for how in ("default", "windows_always"):
+            pop.run(nsteps, how)
+            pop.sp.check(how)
+            ms = _timed(lambda: pop.run(nsteps, how), reps, flush)
+            pop.sp.check(how)
+            row[how] = {"agent_steps_per_s": n * nsteps / (ms / 1e3), "ms_per_step": ms / nsteps}
+        cand, cont, boxes = candidates_and_contacts(U, pop.x0, prm)
+        alg = BYTES_PER_AGENT_STEP * n + BYTES_PER_BOX * boxes
+        row.update({"contacts_per_agent_initial": cont, "candidates_per_agent_initial": cand,
+                    "step_hbm_frac": alg / (row["default"]["ms_per_step"] / 1e3) / 1e9 / hbm,
+                    "kernel_us_per_step_traced": kernel_split(pop, nsteps)})
+        out[name] = row
+    return out
 
 
 def measure_batched(dev, flush, nsims=256, nsteps=50, reps=3):
     """256 independent simulations (agent counts log-uniform in [1e3, 2e5], mean
-    neighbours U[4, 40]), 50 steps: the batched step captured as one CUDA graph
-    versus the 256 simulations run one after another with the plain step of
-    the same method (ug_step, or ug_step_pairs_once when the tuner picks every
-    pair once)."""
+    neighbours U[4, 40]), 50 steps: the batched step as one CUDA graph (the
+    library's BatchedGraph) against the 256 simulations run one after another
+    with the plain step of the same method, both as one CUDA graph and launched
+    call by call."""
     import torch
 
     from paper_2105_00039_gb300 import populations as P
@@ -463,24 +635,12 @@ def measure_batched(dev, flush, nsims=256, nsteps=50, reps=3):
         x.copy_(x0)
         U._check(lib.ug_iota(U._ptr(perm), n, U._stream()), "ug_iota")
 
-    def batched():
-        sp.step_batched(x, perm, offs_t, pdev, nsteps, tune)
-
-    s = torch.cuda.Stream(device=dev)
-    s.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(s):
-        reset()
-        batched()                                  # warm-up outside capture
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=s):
-            batched()
-    torch.cuda.current_stream().wait_stream(s)
-    torch.cuda.synchronize()
+    reset()
+    graph = U.BatchedGraph(sp, x, perm, offs_t, pdev, nsteps, tune)
 
     def run_graph():
         reset()
-        g.replay()
+        graph.replay()
     run_graph()
     sp.check("batched")
     t_batched = _timed(run_graph, reps, flush)
@@ -501,11 +661,29 @@ def measure_batched(dev, flush, nsims=256, nsteps=50, reps=3):
     for k in range(0, nsims, 37):
         steppers[k].check("sequential")
     same = all(torch.equal(x[int(offs[k]):int(offs[k + 1])], xs[k]) for k in range(nsims))
+    # the same sequential runs captured as one CUDA graph (launch overhead removed)
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(torch.cuda.current_stream())
+    gseq = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(gseq, stream=side):
+            sequential()
+    torch.cuda.current_stream().wait_stream(side)
+    gseq.replay()
+    torch.cuda.synchronize()
+    t_seq_graph = _timed(gseq.replay, reps, flush)
+    for k in range(0, nsims, 37):
+        steppers[k].check("sequential graph")
+    same_graph = all(torch.equal(x[int(offs[k]):int(offs[k + 1])], xs[k]) for k in range(nsims))
     return {"workload": f"{nsims} simulations, {n} agents in total, {nsteps} steps",
             "batched_graph_ms": t_batched, "sequential_plain_ms": t_seq,
+            "sequential_graph_ms": t_seq_graph,
             "batched_agent_steps_per_s": n * nsteps / (t_batched / 1e3),
             "sequential_agent_steps_per_s": n * nsteps / (t_seq / 1e3),
-            "speedup": t_seq / t_batched, "bit_identical_to_plain": bool(same),
+            "sequential_graph_agent_steps_per_s": n * nsteps / (t_seq_graph / 1e3),
+            "speedup_vs_sequential_calls": t_seq / t_batched,
+            "speedup_vs_sequential_graph": t_seq_graph / t_batched,
+            "bit_identical_to_plain": bool(same and same_graph),
             "tuned_sweep_block": int(tune.sweep_block),
             "tuned_agents_per_lane": int(tune.agents_per_lane),
             "tuned_pair_mode": int(tune.pair_mode)}
@@ -561,48 +739,14 @@ def measure_adjoint(dev, flush, side=64, nsteps=50, ckpt=10, reps=3):
             "backward_over_forward": b_ms / f_ms, "backward_over_plain_forward": b_ms / p_ms}
 
 
-def measure_lattice_margin(dev, flush, margin=1.5, nsteps=100, reps=2):
-    """The headline lattice with each contact radius widened by a margin of 1.5
-    (the variant that reaches ~12 overlapping neighbours per cell), 100 fused
-    steps: agent-steps/s and the measured mean neighbour count."""
-    import torch
-
-    from paper_2105_00039_gb300 import populations as P
-    from paper_2105_00039_gb300 import ugmech as U
-    st = P.lattice_1m(0)
-    n = len(st)
-    x0 = torch.from_numpy(st).to(dev)
-    prm = U.Params(contact_margin=margin)
-    mb = U.estimate_max_boxes(x0, margin, slack=1.2)
-    sp = U.Stepper(n, mb, dev)
-    x = torch.empty_like(x0)
-    perm = torch.empty(n, dtype=torch.int32, device=dev)
-    lib = U.load()
-
-    def run():
-        x.copy_(x0)
-        U._check(lib.ug_iota(U._ptr(perm), n, U._stream()), "ug_iota")
-        sp.step(x, perm, prm, nsteps)
-    run()
-    sp.check("lattice margin")
-    ms = _timed(run, reps, flush)
-    sp.check("lattice margin")
-    srt, _, start, info, _ = U.grid_build(x0, contact_margin=margin)
-    F = U.compute_forces(srt, start, info, prm)
-    return {"workload": f"lattice_1m with contact margin {margin}, {nsteps} fused steps",
-            "agent_steps_per_s": n * nsteps / (ms / 1e3), "ms_per_step": ms / nsteps,
-            "mean_neighbours_initial": float(F[:, 3].double().mean().item())}
-
-
 def measure_pairs_once(dev, flush, reps=5):
     """Newton's third law (ug_forces_symmetric) on the box-sorted 2^20-cell
     lattice: one force evaluation with every pair evaluated once (forward half
     of each neighbourhood, fixed-point atomics to both agents), the same walk
     over all 27 boxes, and the main path's force sweep (ug_compute_forces)."""
-    import torch
-
     from paper_2105_00039_gb300 import populations as P
     from paper_2105_00039_gb300 import ugmech as U
+    import torch
     x = torch.from_numpy(P.lattice_1m(0)).to(dev)
     n = x.shape[0]
     prm = U.Params()
@@ -683,70 +827,6 @@ def measure_ladder(dev, flush, reps=3):
     U.check_status(status, "main path")
     out["main_path_grid_build_plus_forces"] = {"ms": ms, "agents_per_s": n / (ms / 1e3)}
     return out
-
-
-def measure_density(dev, flush, reps=2, nsteps=20):
-    """Benchmark-B style density sweep: uniform centres in cubes sized for a mean
-    of 2, 8, 32, 64 overlapping neighbours (4,194,304 cells) and 12 (16,777,216
-    cells), max displacement 0 (frozen), 20 steps each, with ug_step and with
-    ug_step_pairs_once."""
-    import torch
-
-    from paper_2105_00039_gb300 import populations as P
-    from paper_2105_00039_gb300 import ugmech as U
-    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-        hbm = float(json.load(f)["hbm_gbs"])
-    prm = U.Params(max_disp=0.0)
-    rows = []
-    lib = U.load()
-    for n, nbar in ((1 << 22, 2), (1 << 22, 8), (1 << 22, 32), (1 << 22, 64), (1 << 24, 12)):
-        st = P.density_cube(n, float(nbar), seed=nbar)
-        x0 = torch.from_numpy(st).to(dev)
-        del st
-        mb = U.estimate_max_boxes(x0, 0.0, slack=1.05)
-        sp = U.Stepper(n, mb, dev)
-        x = torch.empty_like(x0)
-        perm = torch.empty(n, dtype=torch.int32, device=dev)
-
-        def run(pairs_once=False):
-            x.copy_(x0)
-            U._check(lib.ug_iota(U._ptr(perm), n, U._stream()), "ug_iota")
-            sp.step(x, perm, prm, nsteps, pairs_once=pairs_once)
-        run(); sp.check("density"); torch.cuda.synchronize()
-        ms = _timed(run, reps, flush)
-        sp.check("density")
-        # the same steps with every pair evaluated once (ug_step_pairs_once)
-        run(True); sp.check("density, pairs once"); torch.cuda.synchronize()
-        ms_once = _timed(lambda: run(True), reps, flush)
-        sp.check("density, pairs once")
-        per_step_s = ms / 1e3 / nsteps
-        alg = BYTES_PER_AGENT_STEP * n + BYTES_PER_BOX * mb / 1.05
-        # one traced pass for the per-kernel split (events un-chain the kernels)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 + 5 * nsteps)]
-        for e in ev:
-            e.record()
-        x.copy_(x0)
-        U._check(lib.ug_iota(U._ptr(perm), n, U._stream()), "ug_iota")
-        sp.step_traced(x, perm, prm, nsteps, ev)
-        ev[-1].synchronize()
-        names = ("key", "scan", "place", "canon", "sweep")
-        split = {nm: sum(ev[1 + 5 * t + j].elapsed_time(ev[2 + 5 * t + j]) for t in range(nsteps))
-                 * 1000.0 / nsteps for j, nm in enumerate(names)}
-        # the sweep against the FP32 ALU roof (the population is frozen: counts hold every step)
-        cand, cont = candidates_and_contacts(U, x0, prm)
-        flops = n * (FLOPS_PER_CANDIDATE * cand + FLOPS_PER_CONTACT * cont + FLOPS_PER_AGENT)
-        tflops = flops / (split["sweep"] * 1e-6) / 1e12
-        rows.append({"n_agents": n, "mean_neighbours_target": nbar,
-                     "agent_steps_per_s": n * nsteps / (ms / 1e3), "ms_per_step": per_step_s * 1e3,
-                     "step_alg_gbs": alg / per_step_s / 1e9, "step_hbm_frac": alg / per_step_s / 1e9 / hbm,
-                     "pairs_once_agent_steps_per_s": n * nsteps / (ms_once / 1e3),
-                     "pairs_once_ms_per_step": ms_once / nsteps,
-                     "candidates_per_agent": cand, "contacts_per_agent": cont,
-                     "sweep_alu_tflops": tflops, "sweep_alu_frac": tflops / FP32_PEAK_TFLOPS,
-                     "kernel_us_per_step_traced": split})
-        del x0, x, perm, sp
-        torch.cuda.empty_cache()
-    return rows
 
 
 def main():

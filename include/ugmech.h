@@ -117,7 +117,14 @@ typedef struct {
     int32_t sweep_block;      /* 64 or 128; 0 = default (128) */
     int32_t agents_per_lane;  /* 1 or 2; 0 = default (2) */
     int32_t pair_mode;        /* 0 or 1; 0 = default */
-    int32_t reserved[5];
+    int32_t neighbour_walk;   /* with agents_per_lane 2 and pair_mode 0, one simulation:
+                                 0 = each neighbour row cut to the x-window that can hold
+                                 contacts where that pays (grids with 8 x sub-bins per box,
+                                 about 16 neighbours per agent and up), else the full
+                                 three-box runs (default); 1 = always the full runs;
+                                 2 = always the windows.  The same bits every way.
+                                 Several simulations always walk full runs. */
+    int32_t reserved[4];
 } ug_tuning;
 
 /* ------------------------------------------------------------------ workspace */
@@ -152,7 +159,7 @@ int ug_grid_build(const float *state_in, const uint32_t *perm_in, uint32_t n,
  * their inputs and outputs and may not allocate at the point of the call -- a
  * plug-in whose host application owns all of the GPU's memory, or code under a
  * fixed memory budget -- so they cannot supply ug_grid_build's workspace.  This
- * variant uses a fixed scratch array of about 7 MiB compiled into the library
+ * variant uses a fixed scratch array of about 14 MiB compiled into the library
  * (one per GPU that loads it, held until the process exits) and calls no
  * allocator.  Arguments and results are those of ug_grid_build, and its
  * argument checks come first (UG_EINVAL as there).

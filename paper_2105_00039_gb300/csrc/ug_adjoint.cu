@@ -56,7 +56,7 @@ static size_t adj_layout(void *base, uint32_t n, uint32_t max_boxes, int nsteps,
     L->perm = reinterpret_cast<uint32_t *>(take(4 * (size_t)n));
     L->saves.sorted = reinterpret_cast<float4 *>(take(16 * (size_t)n * S));
     L->saves.sigma = reinterpret_cast<uint32_t *>(take(4 * (size_t)n * S));
-    L->saves.start_stride = ((size_t)max_boxes + 1 + 63) & ~(size_t)63;
+    L->saves.start_stride = ((size_t)table_capacity(n, max_boxes) + 1 + 63) & ~(size_t)63;
     L->saves.start = reinterpret_cast<uint32_t *>(take(4 * L->saves.start_stride * S));
     L->saves.force = reinterpret_cast<float4 *>(take(16 * (size_t)n * S));
     L->saves.geo = reinterpret_cast<ug_grid_info *>(take(sizeof(ug_grid_info) * S));

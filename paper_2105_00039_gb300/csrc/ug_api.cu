@@ -37,14 +37,16 @@ size_t layout_workspace(void *base, uint32_t n, uint32_t nsims, uint32_t max_box
         off = align256(off + bytes);
         return p;
     };
+    // the box table has up to table_capacity entries (boxes x their sub-bins)
+    const size_t cap = (size_t)table_capacity(n, max_boxes);
     w->ctrl = reinterpret_cast<Ctrl *>(take(sizeof(Ctrl)));
-    w->ntiles = std::max<uint32_t>(1u, (uint32_t)(((size_t)max_boxes + kScanTile - 1) / kScanTile));
+    w->ntiles = std::max<uint32_t>(1u, (uint32_t)((cap + kScanTile - 1) / kScanTile));
     w->tile_sum = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * kTileSumStride * kTileCopies * (size_t)w->ntiles));
-    w->counts = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (size_t)max_boxes));
+    w->counts = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * cap));
     w->bounds = reinterpret_cast<uint32_t *>(
         take(sizeof(uint32_t) * kBoundsWords * (size_t)bounds_copies(nsims) * nsims));
     const size_t zero_end = off;
-    w->start = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * ((size_t)max_boxes + 1)));
+    w->start = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (cap + 1)));
     w->key = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (size_t)n));
     w->rank = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (size_t)n));
     w->tmp = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (size_t)n));
@@ -67,7 +69,7 @@ static int last_launch() { return cuda_status(cudaGetLastError()); }
 
 int run_steps(float4 *state, uint32_t *perm, const SimArgs &sa, int nsteps, uint32_t max_boxes,
               const Workspace &w, int sweep_block, int agents_per_lane, const StepSaves *saves,
-              int32_t *status, cudaStream_t s, cudaEvent_t const *events) {
+              int32_t *status, cudaStream_t s, cudaEvent_t const *events, bool windowed) {
     const uint32_t n = sa.n;
     auto mark = [&](int k) {
         if (events) cudaEventRecord(events[k], s);
@@ -92,7 +94,7 @@ int run_steps(float4 *state, uint32_t *perm, const SimArgs &sa, int nsteps, uint
         launch_place(w, start, n, status, s);
         mark(4 + 5 * t);
         // the provisional ranks are consumed by the placement kernel, so their
-        // buffer carries the sorted rows' box keys from canon to the sweep
+        // buffer carries the sorted rows' sort keys from canon to the sweep
         launch_canon(w, start, state, pcur, sorted, pnext,
                      saves ? saves->sigma + (size_t)t * n : nullptr, n, status, s, w.rank);
         mark(5 + 5 * t);
@@ -106,7 +108,7 @@ int run_steps(float4 *state, uint32_t *perm, const SimArgs &sa, int nsteps, uint
         if (agents_per_lane == 3)
             launch_sym_step(sorted, start, w.geo, sa, o, w.acc, status, s, w.rank);
         else if (agents_per_lane == 2)
-            launch_sweep2(kSweepStep, sorted, start, w.geo, sa, o, status, s, w.rank);
+            launch_sweep2(kSweepStep, sorted, start, w.geo, sa, o, status, s, w.rank, windowed);
         else
             launch_sweep(kSweepStep, sorted, start, w.geo, sa, o, sweep_block, status, s, w.rank);
         std::swap(pcur, pnext);
@@ -187,12 +189,14 @@ int ug_grid_build(const float *state_in, const uint32_t *perm_in, uint32_t n, fl
     sa.bounds_copies = bounds_copies(1);
     if (cudaMemsetAsync(w.ctrl, 0, zero_bytes(w), s) != cudaSuccess) return UG_ECUDA;
     const float4 *in = reinterpret_cast<const float4 *>(state_in);
-    launch_bounds(in, sa, w, info, max_boxes, status, s);
-    launch_key(in, sa, w, info, nullptr, status, s);
-    launch_scan(w, box_start, max_boxes, status, s);
-    launch_place(w, box_start, n, status, s);
-    launch_canon(w, box_start, in, perm_in, reinterpret_cast<float4 *>(state_sorted), perm_sorted,
+    launch_bounds(in, sa, w, w.geo, max_boxes, status, s);
+    launch_key(in, sa, w, w.geo, nullptr, status, s);
+    launch_scan(w, w.start, max_boxes, status, s);
+    launch_place(w, w.start, n, status, s);
+    launch_canon(w, w.start, in, perm_in, reinterpret_cast<float4 *>(state_sorted), perm_sorted,
                  nullptr, n, status, s);
+    // the caller's per-box table (the first sub-bin entry of every box) and geometry
+    launch_box_table(w.start, w.geo, box_start, info, max_boxes, status, s);
     return last_launch();
 }
 
@@ -206,6 +210,7 @@ int ug_compute_forces(const float *state_sorted, const uint32_t *box_start, cons
     sa.n = n;
     sa.pval = p;
     sa.bounds_copies = 1;
+    sa.per_box_table = true;   // the caller's table from ug_grid_build
     SweepOut o{};
     o.force = reinterpret_cast<float4 *>(force);
     launch_sweep2(kSweepForce, reinterpret_cast<const float4 *>(state_sorted), box_start, info, sa,
@@ -226,6 +231,7 @@ int ug_list_pairs(const float *state_sorted, const uint32_t *box_start, const ug
     sa.n = n;
     sa.pval.contact_margin = contact_margin;
     sa.bounds_copies = 1;
+    sa.per_box_table = true;   // the caller's table from ug_grid_build
     SweepOut o{};
     o.pair_count = count;
     o.nbr = nbr;
@@ -328,13 +334,16 @@ int ug_step_batched(float *state, uint32_t *perm, const uint32_t *sim_offset, ui
     const int block = tuning && tuning->sweep_block ? tuning->sweep_block : 128;
     const int apl = tuning && tuning->agents_per_lane ? tuning->agents_per_lane : 2;
     const int pair_mode = tuning ? tuning->pair_mode : 0;
-    if ((block != 64 && block != 128) || (apl != 1 && apl != 2) || (pair_mode != 0 && pair_mode != 1))
+    const int walk = tuning ? tuning->neighbour_walk : 0;
+    if ((block != 64 && block != 128) || (apl != 1 && apl != 2) || (pair_mode != 0 && pair_mode != 1) ||
+        walk < 0 || walk > 2)
         return UG_EINVAL;
+    sa.windows_always = walk == 2;
     if (pair_mode == 1)   // every pair once: its own kernels, whatever the sweep layout
         return run_steps(reinterpret_cast<float4 *>(state), perm, sa, nsteps, max_boxes, w, 128, 3,
                          nullptr, status, static_cast<cudaStream_t>(stream));
     return run_steps(reinterpret_cast<float4 *>(state), perm, sa, nsteps, max_boxes, w, block, apl,
-                     nullptr, status, static_cast<cudaStream_t>(stream));
+                     nullptr, status, static_cast<cudaStream_t>(stream), nullptr, walk != 1);
 }
 
 int ug_tune_batched(const float *state, const uint32_t *sim_offset, uint32_t nsims, uint32_t n_total,

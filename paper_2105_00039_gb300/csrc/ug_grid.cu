@@ -4,20 +4,26 @@
 // state along a Z-order curve so that neighbours share cache lines.  Here the
 // grid IS the sort: a counting sort by box key, boxes in row-major order (x
 // fastest, so the three boxes of a neighbourhood along x are one contiguous
-// run), agents of a box in their input order.  Five kernels per rebuild:
+// run), agents of a box by x sub-bin (K = 2^ks slices of the box edge along x,
+// ks chosen per simulation from its density; see sort_key) and, within a
+// sub-bin, in their input order.  The table therefore has K entries per box,
+// one per sub-bin.  Five kernels per rebuild:
 //
 //   k_bounds  (first step only; later steps get it from the sweep epilogue)
 //             per-simulation min/max corner and max diameter -> grid geometry
-//   k_key     box key of every row + warp-aggregated atomic histogram; the
-//             atomic's return value is a provisional rank inside the box; the
-//             rows of every scan tile (8192 boxes) are summed on the side
-//   k_scan    exclusive scan of the box counts, one CTA per tile, whose prefix
-//             is the sum of the earlier tiles' row counts (no inter-CTA wait),
-//             also re-zeroing the counts
+//   k_key     sort key (box and x sub-bin) of every row + warp-aggregated
+//             atomic histogram; the atomic's return value is a provisional
+//             rank inside the sub-bin; the rows of every scan tile (8192 table
+//             entries) are summed on the side
+//   k_scan    exclusive scan of the sub-bin counts, one CTA per tile, whose
+//             prefix is the sum of the earlier tiles' row counts (no inter-CTA
+//             wait), also re-zeroing the counts
 //   k_place   row index -> provisional slot; re-zeroes the tile sums
-//   k_canon   stable order inside each box (rank = rows of the box with a
-//             smaller input index), gathering rows and ids into that slot
+//   k_canon   stable order inside each sub-bin (rank = rows of the sub-bin
+//             with a smaller input index), gathering rows and ids into that slot
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "ug_internal.cuh"
 
@@ -77,9 +83,7 @@ k_key(const float4 *__restrict__ st, SimArgs sa, const ug_grid_info *__restrict_
         k[it] = 0xffffffffu;
         if (idx[it] < sa.n) {
             const uint32_t sim = uniform ? csim : find_sim(sa, idx[it]);
-            const ug_grid_info g = geo[sim];
-            int bx, by, bz;
-            k[it] = box_key(p[it], g, bx, by, bz);
+            k[it] = sort_key(p[it], geo[sim]);
         }
         // rows arrive nearly sorted by box (the previous step's order), so equal
         // keys mostly sit on consecutive lanes: each run of equal keys takes one
@@ -265,7 +269,7 @@ k_canon(const uint32_t *__restrict__ tmp, const uint32_t *__restrict__ key,
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
         if (sl[q] >= n) continue;
-        // stable rank inside the box: rows of the box with a smaller input index
+        // stable rank inside the sub-bin: its rows with a smaller input index
         uint32_t r = 0;
         for (uint32_t t = b0[q]; t < b1[q]; ++t) r += __ldg(tmp + t) < id[q];
         const uint32_t dest = b0[q] + r;
@@ -274,6 +278,27 @@ k_canon(const uint32_t *__restrict__ tmp, const uint32_t *__restrict__ key,
         if (sigma) sigma[dest] = id[q];
         if (skey) skey[dest] = k[q];
     }
+}
+
+// ------------------------------------------------------------------ per-box table
+// The table of a single simulation reduced to one entry per box (entry b << ks,
+// the start of the box's first sub-bin; the last entry is n), and its geometry
+// with reserved = 0, which is how callers of the per-box entry points read a
+// box table.  Writes the geometry even after a failed build.
+__global__ void __launch_bounds__(256)
+k_box_table(const uint32_t *__restrict__ table, const ug_grid_info *__restrict__ geo,
+            uint32_t *__restrict__ box_start, ug_grid_info *info, int32_t *status) {
+    chain_begin();
+    const ug_grid_info g = geo[0];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ug_grid_info o = g;
+        o.reserved = 0u;
+        info[0] = o;
+    }
+    if (cta_failed(status)) return;
+    const int ks = grid_shift(g);
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b <= g.nboxes; b += gridDim.x * blockDim.x)
+        box_start[b] = __ldg(table + ((size_t)b << ks));
 }
 
 // ------------------------------------------------------------------ launchers
@@ -311,4 +336,13 @@ void launch_canon(const Workspace &w, const uint32_t *start, const float4 *st_in
                    st_sorted, perm_out, sigma, n, skey, status);
 }
 
+}  // namespace ug
+
+namespace ug {
+void launch_box_table(const uint32_t *table, const ug_grid_info *geo, uint32_t *box_start,
+                      ug_grid_info *info, uint32_t max_boxes, int32_t *status, cudaStream_t s) {
+    const unsigned cap = 4u * (unsigned)device_sm_count();
+    const unsigned blocks = (unsigned)std::min<size_t>(cap, ((size_t)max_boxes + 256) / 256);
+    launch_chained(k_box_table, blocks, 256u, s, table, geo, box_start, info, status);
+}
 }  // namespace ug

@@ -30,7 +30,7 @@ constexpr int kBoundsCopiesSingle = 32;                 // spread atomics when n
 struct Ctrl {
     uint32_t spare;
     uint32_t done;          // CTAs finished (last-CTA pattern of the bounds reduction)
-    uint32_t total_boxes;   // boxes of the current grid (all sims); 0 after an error
+    uint32_t total_boxes;   // box table entries of the current grid (all sims); 0 after an error
     uint32_t adj_done;      // last-CTA counter of the adjoint parameter reduction
     uint32_t pad[4];
 };
@@ -43,7 +43,18 @@ struct SimArgs {
     uint32_t nsims;
     uint32_t n;
     uint32_t bounds_copies;   // copies of the bounds accumulators (atomic spreading)
+    bool per_box_table;       // the box table has one entry per box (a caller's table from
+                              // ug_grid_build): kernels then ignore the geometry's sub-bins
+    bool windows_always;      // neighbour-row windows at every number of sub-bins per box
+                              // (default: only where they pay, see k_sweep2)
 };
+// A simulation's geometry as a kernel uses it (see SimArgs::per_box_table).
+__device__ __forceinline__ ug_grid_info sim_geo(const SimArgs &sa, const ug_grid_info *geo,
+                                                uint32_t s) {
+    ug_grid_info g = geo[s];
+    if (sa.per_box_table) g.reserved = 0u;
+    return g;
+}
 
 // ------------------------------------------------------------------ dependent launch
 // Kernels of one step form a chain on the caller's stream.  Each is launched
@@ -149,22 +160,67 @@ __device__ __forceinline__ float ord_dec(uint32_t e) {
 }
 
 // ------------------------------------------------------------------ grid geometry
-// Box coordinate along one axis: max(floor((p - o) / e), 1), IEEE round-to-nearest
-// subtraction and division (the oracle evaluates the same expression in float32).
-// The upper clamp never binds for rows the geometry was built from.
-__device__ __forceinline__ int box_coord(float p, float o, float e, int dim) {
-    const float f = floorf(__fdiv_rn(__fsub_rn(p, o), e));
-    int b = (int)f;
+// Box coordinate along one axis: max(floor(t), 1) with t = (p - o) / e in IEEE
+// float32 round-to-nearest subtraction and division (the oracle evaluates the
+// same expression in float32).  The upper clamp never binds for rows the
+// geometry was built from.  *t_out gets t itself (the position in box units).
+__device__ __forceinline__ int box_coord(float p, float o, float e, int dim, float *t_out = nullptr) {
+    const float t = __fdiv_rn(__fsub_rn(p, o), e);
+    int b = (int)floorf(t);
     b = max(b, 1);
     b = min(b, dim - 2);
+    if (t_out) *t_out = t;
     return b;
 }
+
+// Agents are ordered by box and, inside a box, by x sub-bin: the box edge is
+// cut into K = 2^ks equal slices along x (sub-bin sx = floor((t_x - b_x) K),
+// clamped into [0, K)), so that the three boxes of a neighbour row, walked in
+// table order, are sorted by x at the resolution e / K and an agent's
+// candidates in that row form a short window (the grid's purpose in Sec. IV-A
+// and IV-D is locality; the finer x order is how this library serves it).
+// K follows the simulation's density: the largest 2^ks <= 8 with
+// 4 * K * boxes <= 5 * agents (about one agent per sub-bin or more), so K = 1
+// for sparse grids.  The box table then holds K entries per box: entry
+// box_base + (box << ks) + sx starts sub-bin sx of the box, and the K entries of a
+// simulation's boxes add up to at most boxes + 1.25 agents.
+constexpr int kSubShiftMax = 3;
+__host__ __device__ __forceinline__ int sub_shift(uint32_t agents, unsigned long long boxes) {
+    int ks = 0;
+    while (ks < kSubShiftMax && 4ull * (boxes << (ks + 1)) <= 5ull * agents) ++ks;
+    return boxes == 0 ? 0 : ks;
+}
+// Entries of a box table serving n agents in grids of at most max_boxes boxes.
+__host__ __device__ __forceinline__ unsigned long long table_capacity(uint32_t n, uint32_t max_boxes) {
+    return (unsigned long long)max_boxes + n + (n >> 2) + 1;
+}
+__device__ __forceinline__ int grid_shift(const ug_grid_info &g) { return (int)g.reserved; }
+
+// Table entry of the first sub-bin of the agent's box (the box key); bx, by, bz
+// get the box coordinates.
 __device__ __forceinline__ uint32_t box_key(const float4 &p, const ug_grid_info &g,
                                             int &bx, int &by, int &bz) {
     bx = box_coord(p.x, g.origin[0], g.edge, g.dims[0]);
     by = box_coord(p.y, g.origin[1], g.edge, g.dims[1]);
     bz = box_coord(p.z, g.origin[2], g.edge, g.dims[2]);
-    return g.box_base + (uint32_t)((bz * g.dims[1] + by) * g.dims[0] + bx);
+    return g.box_base + ((uint32_t)((bz * g.dims[1] + by) * g.dims[0] + bx) << grid_shift(g));
+}
+// Sort key of an agent: its box key plus its x sub-bin.
+__device__ __forceinline__ uint32_t sort_key(const float4 &p, const ug_grid_info &g) {
+    float tx;
+    const int bx = box_coord(p.x, g.origin[0], g.edge, g.dims[0], &tx);
+    const int by = box_coord(p.y, g.origin[1], g.edge, g.dims[1]);
+    const int bz = box_coord(p.z, g.origin[2], g.edge, g.dims[2]);
+    const int ks = grid_shift(g);
+    const int K = 1 << ks;
+    // t_x - b_x is exact (Sterbenz) and scaling by K is exact
+    int sx = (int)floorf(__fmul_rn(__fsub_rn(tx, (float)bx), (float)K));
+    sx = min(max(sx, 0), K - 1);
+    return g.box_base + ((uint32_t)((bz * g.dims[1] + by) * g.dims[0] + bx) << ks) + (uint32_t)sx;
+}
+// The box key of a sort key.
+__device__ __forceinline__ uint32_t box_of_sort_key(uint32_t k, const ug_grid_info &g) {
+    return k - ((k - g.box_base) & ((1u << grid_shift(g)) - 1u));
 }
 
 // ------------------------------------------------------------------ float-float
@@ -272,8 +328,9 @@ __device__ __forceinline__ bool far_from_origin(const float4 &a, float e) {
 
 // ------------------------------------------------------------------ neighbour traversal
 // With boxes numbered x-fastest the 27 boxes around box key k are 9 runs of 3
-// consecutive boxes, one per (dy, dz): run (dy, dz) covers sorted slots
-// start[k + dz*plane + dy*row - 1] .. start[k + dz*plane + dy*row + 2].
+// consecutive boxes, one per (dy, dz): with K table entries per box, row
+// stride R = K dims_x and plane stride K dims_x dims_y, run (dy, dz) covers
+// sorted slots start[k + dz*plane + dy*R - K] .. start[k + dz*plane + dy*R + 2K].
 constexpr int kListCap = 20;
 // The filter's relative band on the squared contact distance: the distance s
 // is scaled by c = 1 + 2^-17 (exact in float32, c^2 > 1 + 2^-16), so the
@@ -309,7 +366,7 @@ __device__ __forceinline__ bool prefilter(const float4 &q, const FilterRow &f) {
 // Visit every candidate j != i of the 27 boxes around row i; `fn(j, row_j)` is
 // called for those passing a float32 distance filter whose 2^-16 relative band
 // keeps every true contact (the exact test is fn's job).
-//   key_i   the row's box key, or 0xffffffff to compute it from the position
+//   key_i   the row's box key (box_key), or 0xffffffff to compute it from the position
 //   w       this warp's candidate lists
 // The 9 runs are visited one after another; inside a run every lane tests its
 // t-th candidate in lockstep (trip count = the warp's longest run), with the
@@ -338,7 +395,9 @@ __device__ __forceinline__ void sweep_neighbours(const float4 *__restrict__ st,
             key = box_key(me, g, bx, by, bz);
         }
     }
-    const int row = g.dims[0], plane = g.dims[0] * g.dims[1];
+    const int ks = grid_shift(g);
+    const int row = g.dims[0] << ks, plane = (g.dims[0] * g.dims[1]) << ks;
+    const uint32_t K = 1u << ks;
     const uint32_t self = valid ? i : 0u;
     const FilterRow fr = make_filter_row(me, m2);
     int cnt = 0;
@@ -358,8 +417,8 @@ __device__ __forceinline__ void sweep_neighbours(const float4 *__restrict__ st,
         int len = 0;
         if (valid) {
             const uint32_t kb = (uint32_t)((int)key + (r / 3 - 1) * plane + (r % 3 - 1) * row);
-            b = __ldg(start + kb - 1);
-            len = (int)(__ldg(start + kb + 2) - b);
+            b = __ldg(start + kb - K);
+            len = (int)(__ldg(start + kb + 2 * K) - b);
             if (len == 0) b = self;
         }
         const int last = max(len - 1, 0);
@@ -471,11 +530,14 @@ struct FinalizeScratch {
     unsigned long long scan[256];
     uint32_t w[kFinalizeChunk][kBoundsWords];
     unsigned long long carry;
+    unsigned long long boxes;   // boxes of all simulations (the max_boxes check)
     int bad;
 };
 
 // Run by the last CTA to finish: turn the bounds into each simulation's grid,
-// assign box ranges, check capacity, and reset the accumulators for next time.
+// choose its x sub-bins, assign its range of the box table, check capacity
+// (boxes against max_boxes, table entries against table_capacity), and reset
+// the accumulators for next time.
 // `fs` may point into shared memory the CTA no longer needs.
 __device__ __forceinline__ void finalize_grid(const SimArgs &sa, uint32_t *bounds,
                                               ug_grid_info *geo, Ctrl *ctrl, uint32_t max_boxes,
@@ -487,7 +549,7 @@ __device__ __forceinline__ void finalize_grid(const SimArgs &sa, uint32_t *bound
     int &s_bad = fs.bad;
     const int tid = threadIdx.x, nt = blockDim.x;
     const uint32_t copies = sa.bounds_copies;
-    if (tid == 0) { s_carry = 0; s_bad = 0; }
+    if (tid == 0) { s_carry = 0; s_bad = 0; fs.boxes = 0; }
     __syncthreads();
     const uint32_t chunk = min(kChunk, (uint32_t)nt);   // one thread per simulation
     for (uint32_t c0 = 0; c0 < sa.nsims; c0 += chunk) {
@@ -544,6 +606,11 @@ __device__ __forceinline__ void finalize_grid(const SimArgs &sa, uint32_t *bound
                 else nb = (unsigned long long)g.dims[0] * g.dims[1] * g.dims[2];
             }
         }
+        // nb: boxes; the table holds K = 2^ks entries per box
+        if (tid < (int)nchunk && nb) atomicAdd(&fs.boxes, nb);
+        const int ks = tid < (int)nchunk ? sub_shift(g.nagents, nb) : 0;
+        const unsigned long long nboxes = nb;
+        nb <<= ks;
         // block exclusive scan of nb (Hillis-Steele on nt <= 256 entries)
         s_scan[tid] = nb;
         __syncthreads();
@@ -557,7 +624,8 @@ __device__ __forceinline__ void finalize_grid(const SimArgs &sa, uint32_t *bound
         const unsigned long long base = s_carry + incl - nb;
         if (tid < (int)nchunk) {
             g.box_base = (uint32_t)min(base, 0xffffffffull);
-            g.nboxes = (uint32_t)nb;
+            g.nboxes = (uint32_t)min(nboxes, 0xffffffffull);
+            g.reserved = (uint32_t)ks;
             geo[s] = g;
         }
         __syncthreads();
@@ -566,9 +634,11 @@ __device__ __forceinline__ void finalize_grid(const SimArgs &sa, uint32_t *bound
     }
     if (tid == 0) {
         if (s_bad) set_status(status, UG_EBADSTATE);
-        const unsigned long long total = s_carry;
-        if (total > (unsigned long long)max_boxes) set_status(status, UG_EGRID_TOO_LARGE);
-        ctrl->total_boxes = (s_bad || total > max_boxes) ? 0u : (uint32_t)total;
+        const unsigned long long total = s_carry;   // table entries
+        const bool too_large = fs.boxes > (unsigned long long)max_boxes ||
+                               total > table_capacity(sa.n, max_boxes);
+        if (too_large) set_status(status, UG_EGRID_TOO_LARGE);
+        ctrl->total_boxes = (s_bad || too_large) ? 0u : (uint32_t)total;
         ctrl->done = 0;
         __threadfence();
     }
@@ -590,8 +660,8 @@ __device__ __forceinline__ bool elect_last_cta(uint32_t *counter) {
 
 // ------------------------------------------------------------------ workspace
 struct Workspace {
-    uint32_t *counts;      // [max_boxes]     zero between steps
-    uint32_t *start;       // [max_boxes + 1]
+    uint32_t *counts;      // [table_capacity]     zero between steps
+    uint32_t *start;       // [table_capacity + 1] the box table (K entries per box)
     uint32_t *key;         // [n]
     uint32_t *rank;        // [n]
     uint32_t *tmp;         // [n]
@@ -634,6 +704,9 @@ void launch_place(const Workspace &w, const uint32_t *start, uint32_t n, int32_t
 void launch_canon(const Workspace &w, const uint32_t *start, const float4 *st_in,
                   const uint32_t *perm_in, float4 *st_sorted, uint32_t *perm_out, uint32_t *sigma,
                   uint32_t n, int32_t *status, cudaStream_t s, uint32_t *skey = nullptr);
+// The caller-facing per-box table and geometry of a single-simulation build.
+void launch_box_table(const uint32_t *table, const ug_grid_info *geo, uint32_t *box_start,
+                      ug_grid_info *info, uint32_t max_boxes, int32_t *status, cudaStream_t s);
 
 // Sweep (ug_sweep.cu).
 enum SweepMode { kSweepForce = 0, kSweepStep = 1, kSweepPairs = 2 };
@@ -656,10 +729,11 @@ void launch_sweep(int mode, const float4 *sorted, const uint32_t *start, const u
 void launch_sym_step(const float4 *sorted, const uint32_t *start, const ug_grid_info *geo,
                      const SimArgs &sa, const SweepOut &out, unsigned long long *acc,
                      int32_t *status, cudaStream_t s, const uint32_t *skey);
-// Two agents per lane (ug_sweep2.cu); single simulation, force or step mode.
+// Two agents per lane (ug_sweep2.cu), force or step mode: one simulation with
+// the windowed walk (windowed) or full neighbour runs, or many simulations.
 void launch_sweep2(int mode, const float4 *sorted, const uint32_t *start, const ug_grid_info *geo,
                    const SimArgs &sa, const SweepOut &out, int32_t *status, cudaStream_t s,
-                   const uint32_t *skey);
+                   const uint32_t *skey, bool windowed = true);
 void launch_apply(const float4 *st_in, const float4 *force, uint32_t n, const ug_params &p,
                   float4 *st_out, float4 *disp_out, int32_t *status, cudaStream_t s);
 
@@ -667,13 +741,14 @@ void launch_apply(const float4 *st_in, const float4 *force, uint32_t n, const ug
 struct StepSaves {          // per-step records for the adjoint (nullable)
     float4 *sorted;         // [nsteps][n]
     uint32_t *sigma;        // [nsteps][n] sorted slot -> input row
-    uint32_t *start;        // [nsteps][start_stride], start_stride >= max_boxes + 1
+    uint32_t *start;        // [nsteps][start_stride], start_stride >= table_capacity + 1
     size_t start_stride;    // entries; a multiple of 64 so every table is 256-byte aligned
     float4 *force;          // [nsteps][n]
     ug_grid_info *geo;      // [nsteps][nsims]
 };
 int run_steps(float4 *state, uint32_t *perm, const SimArgs &sa, int nsteps, uint32_t max_boxes,
               const Workspace &w, int sweep_block, int agents_per_lane, const StepSaves *saves,
-              int32_t *status, cudaStream_t s, cudaEvent_t const *events = nullptr);
+              int32_t *status, cudaStream_t s, cudaEvent_t const *events = nullptr,
+              bool windowed = true);
 
 }  // namespace ug

@@ -8,6 +8,8 @@
 //   version 1  the same in float32 (Sec. IV-C)
 //   version 2  the same over box-sorted rows (Sec. IV-D; the box order of the
 //              main path's counting sort stands in for the Z-order curve)
+//              (the linked lists hold one entry per box, whatever the number
+//              of x sub-bins the main path's box table has per box)
 //   version 3  one CTA per box: the agents of the 27 surrounding boxes are
 //              appended to shared memory through an atomic counter, then the
 //              box's agents are tested against that shared neighbourhood
@@ -35,7 +37,8 @@ k_ll_build(const float4 *__restrict__ rows, uint32_t n, const ug_grid_info *__re
     const ug_grid_info g = geo[0];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int bx, by, bz;
-        const uint32_t k = box_key(__ldg(rows + i), g, bx, by, bz);
+        box_key(__ldg(rows + i), g, bx, by, bz);
+        const uint32_t k = (uint32_t)((bz * g.dims[1] + by) * g.dims[0] + bx);   // one list per box
         next[i] = atomicExch(&head[k], i);
     }
 }
@@ -82,7 +85,7 @@ k_ll_force(const float4 *__restrict__ rows, uint32_t n, const ug_grid_info *__re
     for (int dz = -1; dz <= 1; ++dz)
         for (int dy = -1; dy <= 1; ++dy)
             for (int dx = -1; dx <= 1; ++dx) {
-                const uint32_t key = g.box_base +
+                const uint32_t key =
                     (uint32_t)(((bz + dz) * g.dims[1] + (by + dy)) * g.dims[0] + (bx + dx));
                 for (uint32_t j = __ldg(head + key); j != kNone; j = __ldg(next + j)) {
                     if (++links > n) { set_status(status, UG_EBADSTATE); return; }
@@ -109,18 +112,21 @@ k_box_shared(const float4 *__restrict__ rows, const uint32_t *__restrict__ start
     __shared__ uint32_t s_cnt;
     if (cta_failed(status)) return;
     const ug_grid_info g = geo[0];
-    const uint32_t total = *(volatile const uint32_t *)&ctrl->total_boxes;
+    // boxes of the grid (0 after a failed build); box b's rows are table
+    // entries b K .. (b + 1) K, K = 2^ks x sub-bins per box
+    const uint32_t total = *(volatile const uint32_t *)&ctrl->total_boxes ? g.nboxes : 0u;
+    const int ks = grid_shift(g);
     const float m2 = 2.0f * P.contact_margin;
     const int t = threadIdx.x;
     for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
-        const uint32_t a0 = __ldg(start + b), a1 = __ldg(start + b + 1);
+        const uint32_t a0 = __ldg(start + (b << ks)), a1 = __ldg(start + ((b + 1) << ks));
         if (a0 == a1) continue;   // CTA-uniform: only boxes with agents (always interior)
         if (t == 0) s_cnt = 0u;
         __syncthreads();
         if (t < 27) {
             const int off = (t / 9 - 1) * g.dims[0] * g.dims[1] + (t / 3 % 3 - 1) * g.dims[0] + (t % 3 - 1);
             const uint32_t kb = (uint32_t)((int)b + off);
-            const uint32_t j0 = __ldg(start + kb), j1 = __ldg(start + kb + 1);
+            const uint32_t j0 = __ldg(start + (kb << ks)), j1 = __ldg(start + ((kb + 1) << ks));
             for (uint32_t j = j0; j < j1; ++j) {
                 const uint32_t slot = atomicAdd(&s_cnt, 1u);
                 if (slot < (uint32_t)kLadderShared) {

@@ -7,7 +7,7 @@
 // under a fixed memory budget.  Such a caller cannot supply the workspace that
 // ug_grid_build asks for, so this variant brings its own.
 //
-// The array (kScratchBytes, about 7 MiB) is a file-scope __device__ variable:
+// The array (kScratchBytes, about 14 MiB) is a file-scope __device__ variable:
 // every GPU that loads the library holds one copy until the process exits.  Its
 // device address is looked up with cudaGetSymbolAddress the first time a call
 // runs in a given CUDA context (with that context's device current) and cached
@@ -31,15 +31,20 @@ constexpr uint32_t kNoAllocMaxAgents = 1u << 18;   // 262,144 agents
 constexpr uint32_t kNoAllocMaxBoxes = 1u << 20;    // 1,048,576 grid boxes
 constexpr size_t kAlign = 256;
 constexpr size_t up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
-constexpr size_t kNoAllocTiles = (kNoAllocMaxBoxes + ug::kScanTile - 1) / ug::kScanTile;
-// ctrl | bounds | tile sums | counts | key | rank | tmp.  Every call clears the
-// control words, the bounds, the tile sums of its own scan tiles and the counts
-// of its own max_boxes boxes; the rest is written before it is read.
+// entries of the box table at the limits (boxes times their x sub-bins)
+constexpr size_t kNoAllocTable = (size_t)kNoAllocMaxBoxes + kNoAllocMaxAgents + (kNoAllocMaxAgents >> 2) + 1;
+constexpr size_t kNoAllocTiles = (kNoAllocTable + ug::kScanTile - 1) / ug::kScanTile;
+// ctrl | bounds | tile sums | counts | table | geometry | key | rank | tmp.
+// Every call clears the control words, the bounds, the tile sums of its own
+// scan tiles and the counts of its own table; the rest is written before it is
+// read.
 constexpr size_t kOffBounds = up(sizeof(ug::Ctrl));
 constexpr size_t kOffTiles = kOffBounds + up(4ull * ug::kBoundsWords * ug::kBoundsCopiesSingle);
 constexpr size_t kTileBytes = 4ull * ug::kTileSumStride * ug::kTileCopies;   // per scan tile
 constexpr size_t kOffCounts = kOffTiles + up(kTileBytes * kNoAllocTiles);
-constexpr size_t kOffKey = kOffCounts + up(4ull * kNoAllocMaxBoxes);
+constexpr size_t kOffTable = kOffCounts + up(4ull * kNoAllocTable);
+constexpr size_t kOffGeo = kOffTable + up(4ull * (kNoAllocTable + 1));
+constexpr size_t kOffKey = kOffGeo + up(sizeof(ug_grid_info));
 constexpr size_t kOffRank = kOffKey + up(4ull * kNoAllocMaxAgents);
 constexpr size_t kOffTmp = kOffRank + up(4ull * kNoAllocMaxAgents);
 constexpr size_t kScratchBytes = kOffTmp + up(4ull * kNoAllocMaxAgents);
@@ -133,18 +138,21 @@ extern "C" int ug_grid_build_noalloc(const float *state_in, const uint32_t *perm
     w.ctrl = reinterpret_cast<Ctrl *>(b);
     w.counts = reinterpret_cast<uint32_t *>(b + kOffCounts);
     w.bounds = reinterpret_cast<uint32_t *>(b + kOffBounds);
+    w.start = reinterpret_cast<uint32_t *>(b + kOffTable);
+    w.geo = reinterpret_cast<ug_grid_info *>(b + kOffGeo);
     w.key = reinterpret_cast<uint32_t *>(b + kOffKey);
     w.rank = reinterpret_cast<uint32_t *>(b + kOffRank);
     w.tmp = reinterpret_cast<uint32_t *>(b + kOffTmp);
     w.tile_sum = reinterpret_cast<uint32_t *>(b + kOffTiles);
-    w.ntiles = (max_boxes + kScanTile - 1) / kScanTile;
+    const size_t table = (size_t)table_capacity(n, max_boxes);
+    w.ntiles = (uint32_t)((table + kScanTile - 1) / kScanTile);
     w.bytes = kScratchBytes;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // tile sums and counts must start at zero; the previous call left them zero
     // unless it failed part-way, so clear them (as far as this call uses them)
     // with the control words and the bounds
     if (cudaMemsetAsync(b, 0, kOffTiles + kTileBytes * w.ntiles, s) != cudaSuccess ||
-        cudaMemsetAsync(b + kOffCounts, 0, 4ull * max_boxes, s) != cudaSuccess)
+        cudaMemsetAsync(b + kOffCounts, 0, 4ull * table, s) != cudaSuccess)
         return UG_ECUDA;
     SimArgs sa{};
     sa.nsims = 1;
@@ -152,11 +160,12 @@ extern "C" int ug_grid_build_noalloc(const float *state_in, const uint32_t *perm
     sa.pval.contact_margin = contact_margin;
     sa.bounds_copies = kBoundsCopiesSingle;
     const float4 *in = reinterpret_cast<const float4 *>(state_in);
-    launch_bounds(in, sa, w, info, max_boxes, status, s);
-    launch_key(in, sa, w, info, nullptr, status, s);
-    launch_scan(w, box_start, max_boxes, status, s);
-    launch_place(w, box_start, n, status, s);
-    launch_canon(w, box_start, in, perm_in, reinterpret_cast<float4 *>(state_sorted), perm_sorted,
+    launch_bounds(in, sa, w, w.geo, max_boxes, status, s);
+    launch_key(in, sa, w, w.geo, nullptr, status, s);
+    launch_scan(w, w.start, max_boxes, status, s);
+    launch_place(w, w.start, n, status, s);
+    launch_canon(w, w.start, in, perm_in, reinterpret_cast<float4 *>(state_sorted), perm_sorted,
                  nullptr, n, status, s);
+    launch_box_table(w.start, w.geo, box_start, info, max_boxes, status, s);
     return cudaGetLastError() == cudaSuccess ? UG_OK : UG_ECUDA;
 }

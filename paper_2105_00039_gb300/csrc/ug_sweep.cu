@@ -68,7 +68,9 @@ __device__ __forceinline__ bool sweep_staged(const float4 *__restrict__ st,
     const uint32_t dx = (uint32_t)g.dims[0];
     // invalid lanes (past n) take the last valid lane's box so that they add no row
     const uint32_t k = __shfl_sync(kFull, key, valid ? lane : last_valid);
-    const uint32_t rel = k - g.box_base;
+    const int ks = grid_shift(g);
+    const uint32_t K = 1u << ks;
+    const uint32_t rel = (k - g.box_base) >> ks;
     const uint32_t row = rel / dx;
     const int bx = (int)(rel - row * dx);
     const uint32_t prev = __shfl_up_sync(kFull, row, 1);
@@ -85,9 +87,9 @@ __device__ __forceinline__ bool sweep_staged(const float4 *__restrict__ st,
     uint32_t sbeg = 0, slen = 0;
     if (lane < 9 * R) {
         const int dz = sm / 3 - 1, dy = sm % 3 - 1;
-        const uint32_t kr = g.box_base + (uint32_t)((int)srow + dz * g.dims[1] + dy) * dx;
-        sbeg = __ldg(start + kr + lo - 1);
-        slen = __ldg(start + kr + hi + 2) - sbeg;
+        const uint32_t kr = g.box_base + (((uint32_t)((int)srow + dz * g.dims[1] + dy) * dx) << ks);
+        sbeg = __ldg(start + kr + ((uint32_t)(lo - 1) << ks));
+        slen = __ldg(start + kr + ((uint32_t)(hi + 2) << ks)) - sbeg;
     }
     uint32_t soff = slen;
 #pragma unroll
@@ -106,7 +108,7 @@ __device__ __forceinline__ bool sweep_staged(const float4 *__restrict__ st,
     // this lane's runs, as offsets into the staged rows (an empty run points
     // at the lane's own row, which the j != i test rejects)
     const float4 me = valid ? me_in : make_float4(1e30f, 1e30f, 1e30f, 1.f);
-    const int plane = g.dims[0] * g.dims[1];
+    const uint32_t plane = ((uint32_t)g.dims[0] * (uint32_t)g.dims[1]) << ks, rowk = dx << ks;
     uint32_t self = 0;
     {
         const uint32_t b4 = __shfl_sync(kFull, sbeg, myrow * 9 + 4);
@@ -119,8 +121,8 @@ __device__ __forceinline__ bool sweep_staged(const float4 *__restrict__ st,
         const uint32_t b = __shfl_sync(kFull, sbeg, sg), o = __shfl_sync(kFull, soff, sg);
         uint32_t packed = self | (self << 16);
         if (valid) {
-            const uint32_t kb = (uint32_t)((int)key + (r / 3 - 1) * plane + (r % 3 - 1) * (int)dx);
-            const uint32_t rb = __ldg(start + kb - 1), re = __ldg(start + kb + 2);
+            const uint32_t kb = key + (uint32_t)(r / 3 - 1) * plane + (uint32_t)(r % 3 - 1) * rowk;
+            const uint32_t rb = __ldg(start + kb - K), re = __ldg(start + kb + 2u * K);
             if (re > rb) packed = (o + (rb - b)) | ((o + (re - b)) << 16);
         }
         w.runs[r][lane] = packed;
@@ -175,7 +177,7 @@ k_sweep(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     bool uniform;
     const uint32_t sim = cta_sim(sa, first, i, uniform);
     const ug_params P = sim_params(sa, sim);
-    const ug_grid_info g = geo[sim];
+    const ug_grid_info g = sim_geo(sa, geo, sim);
     const float m2 = 2.0f * P.contact_margin;
     WarpSmem &ws = wsm[threadIdx.x >> 5];
 
@@ -207,7 +209,7 @@ k_sweep(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
         uint32_t key_i = 0u;
         if (valid) {
             if (skey != nullptr) {
-                key_i = __ldg(skey + i);
+                key_i = box_of_sort_key(__ldg(skey + i), g);
             } else {
                 int bx, by, bz;
                 key_i = box_key(me, g, bx, by, bz);
@@ -217,7 +219,7 @@ k_sweep(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
                             [&](const float4 &q) { on_candidate(q); });
     }
     if (!done) {
-        const uint32_t key_i = (skey != nullptr && valid) ? __ldg(skey + i) : 0xffffffffu;
+        const uint32_t key_i = (skey != nullptr && valid) ? box_of_sort_key(__ldg(skey + i), g) : 0xffffffffu;
         sweep_neighbours(st, start, g, i, valid, me, key_i, m2, ws.gl,
                          [&](uint32_t jj, const float4 &q) {
             const uint32_t before = np;

@@ -2,14 +2,18 @@
 //
 // Lane l of the grid handles the box-sorted agents 2l and 2l+1.  Consecutive
 // agents usually share a box or sit in adjacent boxes of one row, so for each
-// of the 9 neighbour rows the two agents' candidate runs merge into one run,
-// boxes [bx(2l) - 1, bx(2l+1) + 1]: every candidate row is loaded once and
-// tested against both agents, which halves the per-candidate index, load and
-// loop work of the one-agent-per-lane sweep.  A lane whose two agents lie too
-// far apart in box order to merge walks the two 9-run sets one after the
-// other.  Runs are walked in warp lockstep (trip count = the warp's longest
-// run; k_sweep2 concatenates the three runs of each neighbour plane) with
-// clamped indices and masks, candidates that pass the packed float32
+// of the 9 neighbour rows the two agents' candidate runs merge into one run:
+// every candidate row is loaded once and tested against both agents, which
+// halves the per-candidate index, load and loop work of the one-agent-per-lane
+// sweep.  A lane whose two agents lie too far apart in box order to merge walks
+// the two 9-run sets one after the other.  In k_sweep2 with WIN (the fused
+// step's default for one simulation) each run of a grid with 8 x sub-bins per
+// box is cut to the agents' x-windows (see row_window); otherwise a run is the
+// row's three boxes.  Runs are walked in
+// warp lockstep (k_sweep2 concatenates the three runs of each neighbour plane,
+// so the trip count is the warp's longest concatenation) with clamped indices
+// and masks; neighbouring lanes read the same candidate rows at the same time,
+// which the L1 serves once.  Candidates that pass the packed float32
 // pre-filter go to per-agent lists, and the exact float-float contact test and
 // Eq. 1 run in warp-converged batches.  k_sweep2 serves one simulation;
 // k_sweep2m serves many (a lane whose agents belong to different simulations
@@ -111,7 +115,8 @@ __device__ __noinline__ void flush_lists2m(const float4 *__restrict__ st, const 
 }
 
 // The two agents' windows merge into one run per neighbour row, boxes
-// [k0 - 1, k1 + 1] shifted by the row's offset, when no two of the 9 merged
+// [k0 - 1, k1 + 1] shifted by the row's offset (box keys; the table has
+// K = 2^ks entries per box, so in table entries k0 - K .. k1 + 2K), when no two of the 9 merged
 // runs can overlap: the 9 offsets are at least one x-row (dims_x boxes) apart,
 // so runs of k1 - k0 + 3 boxes stay disjoint while k1 - k0 <= dims_x - 3.
 // That holds for two agents of one x-row and for the usual pair that straddles
@@ -121,11 +126,68 @@ __device__ __noinline__ void flush_lists2m(const float4 *__restrict__ st, const 
 // there.  The order in which an agent meets
 // its contacts is the same merged or split: ascending within each run, runs in
 // the same order.
-__device__ __forceinline__ bool mergeable(uint32_t k0, uint32_t k1, uint32_t dx) {
-    return k1 >= k0 && k1 - k0 + 3u <= dx;
+__device__ __forceinline__ bool mergeable(uint32_t k0, uint32_t k1, uint32_t dx, int ks) {
+    return k1 >= k0 && ((k1 - k0) >> ks) + 3u <= dx;
 }
 
-template <int MODE, int T>
+// ------------------------------------------------------------------ neighbour-row windows
+// With K = 2^ks table entries per box (x sub-bins, see sort_key) the three boxes
+// of a neighbour row are sorted by x at resolution e / K.  An agent's contacts
+// in row (dy, dz) lie within
+//   |x_j - x_i| < w,  w^2 = S_i^2 - g_y^2 - g_z^2,
+// where S_i >= r_i + r_j + 2m for every j (r_i + m + e / 2, as e >= d_max + 2m)
+// and g_y, g_z are the distances from the agent to that row's faces (0 for its
+// own row or plane), so the row's candidates are the sub-bins overlapping
+// [x_i - w, x_i + w]: two table reads give the window.  Everything is done in
+// box units, t = (p - o) / e exactly as the sort computes it, with slack for
+// its rounding (t carries at most 2^-23 relative error, so every window is
+// widened by (dims + 2) 2^-20 box units and the gaps narrowed by as much) and
+// S_i inflated by 2^-14, so no contact is ever outside its window.  A row with
+// w^2 <= 0 holds no candidate.  Contacts are met in the same order as over the
+// full runs (rows by (dz, dy), ascending slots), so the sums are the same bits.
+// Windows pay where candidates dominate: measured on GB300 (4M cells), they
+// cost more than they save at 2 and 8 neighbours per agent and save 12% at 32,
+// so a grid uses them when it has 8 sub-bins per box (6.4 agents per box or
+// more, about 16 neighbours and up); coarser grids walk the full runs.
+constexpr int kWindowShift = 3;
+constexpr float kWinInflate = 1.0f + 1.0f / 16384.0f;   // on S_i / e
+constexpr float kWinRootInflate = 1.0f + 1.0f / 1048576.0f;   // on the approximate root
+constexpr float kWinSlack = 1.0f / 1048576.0f;           // box units per box of extent
+
+// An agent's place in the grid, in box units.
+struct AgentBox {
+    float tx, fy, fz;   // x position; fractional y and z positions in the box
+    float su;           // largest contact distance / e, inflated
+    int bx, by, bz;
+};
+__device__ __forceinline__ AgentBox agent_box(const float4 &p, const ug_grid_info &g, float inv_e,
+                                              float m) {
+    AgentBox a;
+    float ty, tz;
+    a.bx = box_coord(p.x, g.origin[0], g.edge, g.dims[0], &a.tx);
+    a.by = box_coord(p.y, g.origin[1], g.edge, g.dims[1], &ty);
+    a.bz = box_coord(p.z, g.origin[2], g.edge, g.dims[2], &tz);
+    a.fy = fminf(fmaxf(__fsub_rn(ty, (float)a.by), 0.0f), 1.0f);   // exact for rows of the grid
+    a.fz = fminf(fmaxf(__fsub_rn(tz, (float)a.bz), 0.0f), 1.0f);
+    a.su = (0.5f + (0.5f * p.w + m) * inv_e) * kWinInflate;
+    return a;
+}
+
+// Sub-bins [lo, hi] along the row (dy, dz) of the agent's box that can hold
+// its contacts; false when none can.
+__device__ __forceinline__ bool row_window(const AgentBox &a, int dy, int dz, float sly, float slz,
+                                           float slx, float Kf, int K, int &lo, int &hi) {
+    const float gy = dy == 0 ? 0.0f : fmaxf((dy < 0 ? a.fy : 1.0f - a.fy) - sly, 0.0f);
+    const float gz = dz == 0 ? 0.0f : fmaxf((dz < 0 ? a.fz : 1.0f - a.fz) - slz, 0.0f);
+    const float w2 = a.su * a.su - gy * gy - gz * gz;
+    if (!(w2 > 0.0f)) return false;
+    const float wx = w2 * rsqrtf(w2) * kWinRootInflate + slx;
+    lo = max((int)floorf((a.tx - wx) * Kf), (a.bx - 1) * K);
+    hi = min((int)floorf((a.tx + wx) * Kf), (a.bx + 1) * K + K - 1);
+    return lo <= hi;
+}
+
+template <int MODE, int T, bool WIN>
 __global__ void __launch_bounds__(T, 8)
 k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
          const ug_grid_info *__restrict__ geo, const uint32_t *__restrict__ skey, SimArgs sa,
@@ -138,22 +200,38 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     const uint32_t n = sa.n;
     const uint32_t i0 = (blockIdx.x * T + threadIdx.x) * 2u, i1 = i0 + 1u;
     const bool v0 = i0 < n, v1 = i1 < n;
-    const ug_params P = sa.pval;
-    const ug_grid_info g = geo[0];
+    const ug_params P = sim_params(sa, 0);   // the constants as a single or batched call passes them
+    const ug_grid_info g = sim_geo(sa, geo, 0);
     const float m2 = 2.0f * P.contact_margin;
     const float4 far = make_float4(1e30f, 1e30f, 1e30f, 1.0f);
     const float4 me0 = v0 ? __ldg(st + i0) : far;
     const float4 me1 = v1 ? __ldg(st + i1) : far;
+    const int ks = grid_shift(g);
+    const uint32_t dx = (uint32_t)g.dims[0], dimy = (uint32_t)g.dims[1];
+    const uint32_t K = 1u << ks, R = dx << ks;                   // table entries per box, per row
+    const uint32_t plane = ((uint32_t)g.dims[0] * (uint32_t)g.dims[1]) << ks;
     uint32_t k0 = 0, k1 = 0;
+    const bool win = WIN && (ks >= kWindowShift || sa.windows_always);   // uniform over the grid
+    AgentBox ab0{}, ab1{};   // win: the agents' places in the grid (the sort's own arithmetic)
+    const float inv_e = win ? __frcp_rn(g.edge) : 0.0f;
     if (v0) {
-        int bx, by, bz;
-        k0 = skey ? __ldg(skey + i0) : box_key(me0, g, bx, by, bz);
-        k1 = k0;
-        if (v1) k1 = skey ? __ldg(skey + i1) : box_key(me1, g, bx, by, bz);
+        if (win) {
+            ab0 = agent_box(me0, g, inv_e, P.contact_margin);
+            ab1 = v1 ? agent_box(me1, g, inv_e, P.contact_margin) : ab0;
+            k0 = g.box_base + ((((uint32_t)ab0.bz * dimy + (uint32_t)ab0.by) * dx + (uint32_t)ab0.bx) << ks);
+            k1 = g.box_base + ((((uint32_t)ab1.bz * dimy + (uint32_t)ab1.by) * dx + (uint32_t)ab1.bx) << ks);
+        } else {
+            int bx, by, bz;
+            k0 = skey ? box_of_sort_key(__ldg(skey + i0), g) : box_key(me0, g, bx, by, bz);
+            k1 = k0;
+            if (v1) k1 = skey ? box_of_sort_key(__ldg(skey + i1), g) : box_key(me1, g, bx, by, bz);
+        }
     }
-    const uint32_t dx = (uint32_t)g.dims[0];
-    const int plane = g.dims[0] * g.dims[1];
-    const bool split = v1 && !mergeable(k0, k1, dx);
+    const float slx = (float)(g.dims[0] + 2) * kWinSlack;
+    const float sly = (float)(g.dims[1] + 2) * kWinSlack;
+    const float slz = (float)(g.dims[2] + 2) * kWinSlack;
+    const float Kf = (float)K;
+    const bool split = v1 && !mergeable(k0, k1, dx, ks);
     const bool exact_diffs =
         __all_sync(kFull, (!v0 || far_from_origin(me0, g.edge)) && (!v1 || far_from_origin(me1, g.edge)));
     const FilterPair fp = make_filter_pair(me0, me1, m2);
@@ -211,10 +289,37 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
             if (!split) { lo = k0; hi = k1; s0 = true; s1 = v1; }
             else if (gi < 3) { lo = k0; hi = k0; s0 = true; }
             else { lo = k1; hi = k1; s1 = true; }
-            const uint32_t lz = (uint32_t)((int)lo + dz * plane), hz = (uint32_t)((int)hi + dz * plane);
-            const uint32_t a0 = __ldg(start + lz - dx - 1u), x0 = __ldg(start + hz - dx + 2u);
-            const uint32_t a1 = __ldg(start + lz - 1u), x1 = __ldg(start + hz + 2u);
-            const uint32_t a2 = __ldg(start + lz + dx - 1u), x2 = __ldg(start + hz + dx + 2u);
+            uint32_t a0, x0, a1, x1, a2, x2;
+            if (win) {
+                // each row's run cut to the union of the served agents' windows
+                // (table entries of the sub-bins that can hold their contacts)
+                uint32_t ab[3], xb[3];
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    const int dy = r - 1;
+                    uint32_t wl = 0xffffffffu, wh = 0u;
+                    auto take = [&](const AgentBox &a, uint32_t key) {
+                        int l, h;
+                        if (!row_window(a, dy, dz, sly, slz, slx, Kf, (int)K, l, h)) return;
+                        // the row's first table entry: the key's row shifted by (dy, dz)
+                        const uint32_t rb = key + (uint32_t)dz * plane + (uint32_t)dy * R -
+                                            ((uint32_t)a.bx << ks);
+                        wl = min(wl, rb + (uint32_t)l);
+                        wh = max(wh, rb + (uint32_t)h + 1u);
+                    };
+                    if (s0) take(ab0, k0);
+                    if (s1) take(ab1, k1);
+                    const bool any = wl < wh;
+                    ab[r] = any ? __ldg(start + wl) : 0u;
+                    xb[r] = any ? __ldg(start + wh) : 0u;
+                }
+                a0 = ab[0]; x0 = xb[0]; a1 = ab[1]; x1 = xb[1]; a2 = ab[2]; x2 = xb[2];
+            } else {
+                const uint32_t lz = lo + (uint32_t)dz * plane, hz = hi + (uint32_t)dz * plane;
+                a0 = __ldg(start + lz - R - K); x0 = __ldg(start + hz - R + 2u * K);
+                a1 = __ldg(start + lz - K); x1 = __ldg(start + hz + 2u * K);
+                a2 = __ldg(start + lz + R - K); x2 = __ldg(start + hz + R + 2u * K);
+            }
             e1 = (int)(x0 - a0);
             e2 = e1 + (int)(x1 - a1);
             len = e2 + (int)(x2 - a2);
@@ -299,8 +404,8 @@ k_sweep2m(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     const uint32_t s1 = !MULTI ? 0u : uniform ? s_sims[0] : find_sim(sa, min(i1, n - 1u));
     const ug_params P0 = sim_params(sa, s0);
     const ug_params P1 = s1 == s0 ? P0 : sim_params(sa, s1);
-    const ug_grid_info g0 = geo[s0];
-    const ug_grid_info g1 = s1 == s0 ? g0 : geo[s1];
+    const ug_grid_info g0 = sim_geo(sa, geo, s0);
+    const ug_grid_info g1 = s1 == s0 ? g0 : sim_geo(sa, geo, s1);
     const float m20 = 2.0f * P0.contact_margin, m21 = 2.0f * P1.contact_margin;
     const float4 far = make_float4(1e30f, 1e30f, 1e30f, 1.0f);
     const float4 me0 = v0 ? __ldg(st + i0) : far;
@@ -308,11 +413,11 @@ k_sweep2m(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     uint32_t k0 = 0, k1 = 0;
     if (v0) {
         int bx, by, bz;
-        k0 = skey ? __ldg(skey + i0) : box_key(me0, g0, bx, by, bz);
+        k0 = skey ? box_of_sort_key(__ldg(skey + i0), g0) : box_key(me0, g0, bx, by, bz);
         k1 = k0;
-        if (v1) k1 = skey ? __ldg(skey + i1) : box_key(me1, g1, bx, by, bz);
+        if (v1) k1 = skey ? box_of_sort_key(__ldg(skey + i1), g1) : box_key(me1, g1, bx, by, bz);
     }
-    const bool split = v1 && (s1 != s0 || !mergeable(k0, k1, (uint32_t)g0.dims[0]));
+    const bool split = v1 && (s1 != s0 || !mergeable(k0, k1, (uint32_t)g0.dims[0], grid_shift(g0)));
     const bool exact_diffs = __all_sync(kFull, (!v0 || far_from_origin(me0, g0.edge)) &&
                                                    (!v1 || far_from_origin(me1, g1.edge)));
     const FilterRow f0 = make_filter_row(me0, m20), f1 = make_filter_row(me1, m21);
@@ -339,9 +444,14 @@ k_sweep2m(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
             if (!split) { lo = k0; hi = k1; s0on = true; s1on = v1; }
             else if (r < 9) { lo = k0; hi = k0; s0on = true; }
             else { lo = k1; hi = k1; s1on = true; }
-            const int off = (rr / 3 - 1) * g.dims[0] * g.dims[1] + (rr % 3 - 1) * g.dims[0];
-            b = __ldg(start + (uint32_t)((int)lo + off) - 1u);
-            len = (int)(__ldg(start + (uint32_t)((int)hi + off) + 2u) - b);
+            const int ks = grid_shift(g);
+            const uint32_t K = 1u << ks;
+            const uint32_t off = ((uint32_t)(rr / 3 - 1) * (uint32_t)g.dims[0] * (uint32_t)g.dims[1] +
+                                  (uint32_t)(rr % 3 - 1) * (uint32_t)g.dims[0]) << ks;
+            // indices in 32-bit arithmetic first: off may stand for a negative offset
+            const uint32_t ib = lo + off - K, ie = hi + off + 2u * K;
+            b = __ldg(start + ib);
+            len = (int)(__ldg(start + ie) - b);
             if (len == 0) b = i0;
         }
         const int last = max(len - 1, 0);
@@ -410,7 +520,7 @@ k_sweep2m(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
 
 void launch_sweep2(int mode, const float4 *sorted, const uint32_t *start, const ug_grid_info *geo,
                    const SimArgs &sa, const SweepOut &out, int32_t *status, cudaStream_t s,
-                   const uint32_t *skey) {
+                   const uint32_t *skey, bool windowed) {
     constexpr int T = 128;
     const unsigned grid = (unsigned)((sa.n + 2 * T - 1) / (2 * T));
     if (sa.nsims > 1) {
@@ -420,13 +530,20 @@ void launch_sweep2(int mode, const float4 *sorted, const uint32_t *start, const 
         else
             launch_chained(k_sweep2m<kSweepStep, T, true>, grid, T, s, sorted, start, geo, skey, sa,
                            out, status);
+    } else if (windowed) {
+        if (mode == kSweepForce)
+            launch_chained(k_sweep2<kSweepForce, T, true>, grid, T, s, sorted, start, geo, skey, sa,
+                           out, status);
+        else
+            launch_chained(k_sweep2<kSweepStep, T, true>, grid, T, s, sorted, start, geo, skey, sa,
+                           out, status);
     } else {
         if (mode == kSweepForce)
-            launch_chained(k_sweep2<kSweepForce, T>, grid, T, s, sorted, start, geo, skey, sa, out,
-                           status);
+            launch_chained(k_sweep2<kSweepForce, T, false>, grid, T, s, sorted, start, geo, skey, sa,
+                           out, status);
         else
-            launch_chained(k_sweep2<kSweepStep, T>, grid, T, s, sorted, start, geo, skey, sa, out,
-                           status);
+            launch_chained(k_sweep2<kSweepStep, T, false>, grid, T, s, sorted, start, geo, skey, sa,
+                           out, status);
     }
 }
 

@@ -52,19 +52,22 @@ k_sym(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     // inside one simulation, so the forward walk never leaves it)
     bool uniform;
     const uint32_t sim = cta_sim(sa, blockIdx.x * blockDim.x, i, uniform);
-    const ug_grid_info g = geo[sim];
+    const ug_grid_info g = sim_geo(sa, geo, sim);
     const ug_params P = sim_params(sa, sim);
     const float m2 = 2.0f * P.contact_margin;
     const float4 me = valid ? __ldg(st + i) : make_float4(1e30f, 1e30f, 1e30f, 1.0f);
     uint32_t key = 0;
     if (valid) {
         int bx, by, bz;
-        key = skey ? __ldg(skey + i) : box_key(me, g, bx, by, bz);
+        key = skey ? box_of_sort_key(__ldg(skey + i), g) : box_key(me, g, bx, by, bz);
     }
     const bool exact_diffs = __all_sync(kFull, !valid || far_from_origin(me, g.edge));
     const FilterRow fr = make_filter_row(me, m2);
     const float ri = 0.5f * me.w;
-    const int row = g.dims[0], plane = g.dims[0] * g.dims[1];
+    const int ks = grid_shift(g);
+    const uint32_t K = 1u << ks;
+    const uint32_t row = (uint32_t)g.dims[0] << ks;
+    const uint32_t plane = ((uint32_t)g.dims[0] * (uint32_t)g.dims[1]) << ks;
     long long sx = 0, sy = 0, sz = 0;
     uint32_t np = 0;
     bool overflow = false;
@@ -106,13 +109,13 @@ k_sym(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
         if (valid) {
             if (FORWARD && r == 4) {
                 b = i + 1;
-                len = (int)(__ldg(start + key + 2) - b);
+                len = (int)(__ldg(start + key + 2u * K) - b);
             } else {
                 const int dz = FORWARD ? (r < 3 ? 1 : 0) : r / 3 - 1;
                 const int dy = FORWARD ? (r < 3 ? r - 1 : 1) : r % 3 - 1;
-                const uint32_t kb = (uint32_t)((int)key + dz * plane + dy * row);
-                b = __ldg(start + kb - 1);
-                len = (int)(__ldg(start + kb + 2) - b);
+                const uint32_t kb = key + (uint32_t)dz * plane + (uint32_t)dy * row;
+                b = __ldg(start + kb - K);
+                len = (int)(__ldg(start + kb + 2u * K) - b);
             }
             if (len <= 0) { len = 0; b = i; }
         }
@@ -225,6 +228,7 @@ int run_symmetric(bool forward, const float4 *sorted, const uint32_t *start, con
     sa.n = n;
     sa.pval = p;
     sa.bounds_copies = 1;
+    sa.per_box_table = true;   // the caller's table from ug_grid_build
     const unsigned grid = (unsigned)((n + 127) / 128);
     if (forward)
         k_sym<true, false><<<grid, 128, 0, s>>>(sorted, start, geo, sa, acc, status, nullptr);

@@ -53,7 +53,8 @@ class ug_grid_info(ctypes.Structure):
 
 class ug_tuning(ctypes.Structure):
     _fields_ = [("sweep_block", ctypes.c_int32), ("agents_per_lane", ctypes.c_int32),
-                ("pair_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("pair_mode", ctypes.c_int32), ("neighbour_walk", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 assert ctypes.sizeof(ug_grid_info) == 48
@@ -259,7 +260,7 @@ def grid_info_from_bytes(raw: torch.Tensor) -> dict:
     b = bytes(raw.cpu().numpy().tobytes())
     g = ug_grid_info.from_buffer_copy(b[:48])
     return dict(origin=list(g.origin), edge=g.edge, dims=list(g.dims), box_base=g.box_base,
-                nboxes=g.nboxes, agent_base=g.agent_base, nagents=g.nagents)
+                nboxes=g.nboxes, agent_base=g.agent_base, nagents=g.nagents, reserved=g.reserved)
 
 
 # ------------------------------------------------------------------ entry points
@@ -454,6 +455,37 @@ class Stepper:
 
     def check(self, where="ug_step"):
         check_status(self.status, where)
+
+
+class BatchedGraph:
+    """Many simulations advanced by one CUDA-graph launch: ug_step_batched for
+    nsteps steps, captured once and replayed.
+
+    state, perm, sim_offset and params_dev are the caller's device tensors; the
+    graph reads and writes them in place at every replay (their addresses are
+    fixed at capture, their contents are not), so a caller refills state and
+    perm between replays as it likes.  Construction runs the step once
+    uncaptured on scratch copies (so that every kernel is loaded before the
+    capture) and leaves the caller's tensors untouched.  A replay runs on the
+    current stream; stepper.check() reads the status after it."""
+
+    def __init__(self, stepper: "Stepper", state, perm, sim_offset, params_dev, nsteps: int,
+                 tuning: ug_tuning | None = None):
+        self.stepper = stepper
+        dev = state.device
+        stepper.step_batched(state.clone(), perm.clone(), sim_offset, params_dev, nsteps, tuning)
+        torch.cuda.current_stream(dev).synchronize()
+        stepper.check("BatchedGraph warm-up")
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(self.graph, stream=side):
+                stepper.step_batched(state, perm, sim_offset, params_dev, nsteps, tuning)
+        torch.cuda.current_stream(dev).wait_stream(side)
+
+    def replay(self):
+        self.graph.replay()
 
 
 def iota(n: int, device) -> torch.Tensor:

@@ -59,3 +59,18 @@ def disp_errors(ug, u, S, diam, dt=1.0, density=0.02, exclude=None):
 def ulp32(x):
     x = np.abs(np.asarray(x, np.float32))
     return (np.nextafter(x, np.float32(np.inf)) - x).astype(np.float64)
+
+
+def record(quantity: str, **values):
+    """Append one measured error to the JSON-lines file named by the
+    PARITY_REPORT environment variable (nothing happens when it is unset): the
+    per-quantity error table is assembled from these records."""
+    import json
+    import os
+    path = os.environ.get("PARITY_REPORT")
+    if not path:
+        return
+    row = {"quantity": quantity}
+    row.update({k: (float(v) if isinstance(v, (np.floating, np.integer)) else v) for k, v in values.items()})
+    with open(path, "a") as f:
+        f.write(json.dumps(row) + "\n")

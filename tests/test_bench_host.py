@@ -115,11 +115,17 @@ def test_reference_arm_under_torchrun_two_ranks():
 
 
 def test_issue_roofline(monkeypatch):
+    """The issue view needs a capture of the sweep's current source: without one
+    (or once the source changed) it is null, with one it divides the captured
+    instruction count by the live launch time."""
     sys.path.insert(0, ROOT)
     import bench
+    monkeypatch.setattr(bench, "SWEEP_CAPTURE", {"src": None, "dram_bytes": None, "warp_inst": None})
+    assert bench.issue_roofline(0.1) is None and bench.sweep_capture() is None
+    cap = {"src": bench.sweep_source_hash(), "dram_bytes": 1.0e8, "warp_inst": 2.0e8}
+    monkeypatch.setattr(bench, "SWEEP_CAPTURE", cap)
     r = bench.issue_roofline(0.1)                      # 100 us per launch
-    assert r is not None, "the sweep's source changed since its ncu capture"
-    assert abs(r["achieved_ginst_s"] - bench.SWEEP_WARP_INST / 1e-4 / 1e9) < 1e-6
+    assert abs(r["achieved_ginst_s"] - 2.0e8 / 1e-4 / 1e9) < 1e-6
     assert abs(r["frac"] - r["achieved_ginst_s"] / (152 * 4 * 2.07)) < 1e-12
-    monkeypatch.setattr(bench, "sweep_traffic", lambda: None)
+    monkeypatch.setattr(bench, "SWEEP_CAPTURE", dict(cap, src="0" * 16))
     assert bench.issue_roofline(0.1) is None

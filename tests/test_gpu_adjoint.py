@@ -8,6 +8,8 @@ import torch
 import oracle as O
 from paper_2105_00039_gb300 import populations as P
 
+from _metrics import record
+
 pytestmark = pytest.mark.gpu
 DEV = "cuda"
 TOL = 1e-3
@@ -146,8 +148,52 @@ def test_adjoint_full_size_along_gpu_trajectory(U):
     L, dk, dg, dp, dd = _gpu_grad(U, st, target, U.Params(adherence=0.0), steps, 10)
     states = _gpu_states(U, st, U.Params(adherence=0.0), steps)
     ref = O.trajectory_grad_along(states, target, O.Params(adherence=0.0), "kdtree")
+    record("dL/dkappa (64^3 cells, 50 steps; oracle adjoint along the GPU trajectory)",
+           rel=_rel(dk, ref["dk"]), gpu=dk, oracle=ref["dk"], tolerance=TOL)
+    record("dL/dgamma (64^3 cells, 50 steps; oracle adjoint along the GPU trajectory)",
+           rel=_rel(dg, ref["dgamma"]), gpu=dg, oracle=ref["dgamma"], tolerance=TOL)
+    ep = np.linalg.norm(dp - ref["dpos"], axis=1) / max(np.linalg.norm(ref["dpos"], axis=1).max(), 1e-30)
+    record("dL/dp (64^3 cells, 50 steps; oracle adjoint along the GPU trajectory)",
+           normwise=_nrel(dp, ref["dpos"]), max_row_over_largest=ep.max(), median_row_over_largest=np.median(ep),
+           tolerance=TOL)
+    record("dL/d(diameter) (64^3 cells, 50 steps; oracle adjoint along the GPU trajectory)",
+           normwise=_nrel(dd, ref["ddiam"]), tolerance=TOL)
     assert _rel(dk, ref["dk"]) < TOL and _rel(dg, ref["dgamma"]) < TOL
     assert _nrel(dp, ref["dpos"]) < TOL
+    assert _nrel(dd, ref["ddiam"]) < TOL
+
+
+def test_adjoint_full_size_beside_finite_differences(U):
+    """The differentiable configuration's gradients in k and gamma beside FP64
+    central differences of the oracle's loss at h = 3e-3, 1e-3 and 3e-4 and the
+    oracle's adjoint along its own FP64 trajectory (tests/golden/fd_lattice64.json,
+    written by the oracle alone).  sqrt(delta) puts a kink into the loss
+    wherever a pair starts or stops touching, and 262,144 cells over 50 steps
+    cross many of them, so central differences measure the kinks' jumps as well
+    as the slope: they move with h and sit a few per cent from the adjoint.
+    The GPU's gradient must agree with the oracle adjoint (its float32
+    trajectory crosses slightly different kinks: 2e-2) and lie no farther from
+    the differences than the oracle adjoint itself does (plus that 2e-2)."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "fd_lattice64.json")) as f:
+        gold = json.load(f)
+    steps = 50
+    st, target = _lattice_case(64, steps)
+    L, dk, dg, dp, dd = _gpu_grad(U, st, target, U.Params(adherence=0.0), steps, 10)
+    adj = gold["oracle_adjoint"]
+    rk, rg = _rel(dk, adj["dL_dkappa"]), _rel(dg, adj["dL_dgamma"])
+    for fd in gold["central_differences"]:
+        gk, gg = _rel(dk, fd["dL_dkappa"]), _rel(dg, fd["dL_dgamma"])
+        ok_k, ok_g = _rel(adj["dL_dkappa"], fd["dL_dkappa"]), _rel(adj["dL_dgamma"], fd["dL_dgamma"])
+        record(f"dL/dkappa, dL/dgamma vs FP64 central differences, h = {fd['h']} (64^3 cells, 50 steps)",
+               gpu_kappa=dk, fd_kappa=fd["dL_dkappa"], rel_kappa=gk, oracle_adjoint_rel_kappa=ok_k,
+               gpu_gamma=dg, fd_gamma=fd["dL_dgamma"], rel_gamma=gg, oracle_adjoint_rel_gamma=ok_g)
+        assert gk <= ok_k + 2e-2 and gg <= ok_g + 2e-2
+    record("dL/dkappa, dL/dgamma vs the oracle adjoint along its own FP64 trajectory (64^3, 50 steps)",
+           rel_kappa=rk, rel_gamma=rg, loss_gpu=L, loss_oracle=gold["loss"])
+    assert rk < 2e-2 and rg < 2e-2
+    assert _rel(L, gold["loss"]) < 1e-3
 
 
 def test_backward_is_deterministic_and_zero_steps(U):

@@ -220,6 +220,14 @@ def test_sub_bin_rule_values():
     assert O.sub_bin_shift(10, 0) == 0
 
 
+def test_windowed_walk_test_populations_use_1_to_8_slices():
+    """The populations that tests/test_gpu_windows.py walks both ways cover
+    every number of x slices per box."""
+    from test_gpu_windows import _cases
+    ks = {name: O.grid(st, m)["ks"] for name, (st, m) in _cases().items()}
+    assert {ks["sparse_K1"], ks["lattice_K2"], ks["dense_K4"], ks["dense_K8"]} == {0, 1, 2, 3}
+
+
 def test_grid_slices_hand_example():
     assert check_grid_slices_hand()
 
