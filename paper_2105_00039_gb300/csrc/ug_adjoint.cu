@@ -238,7 +238,8 @@ int ug_step_backward(const float *ckpt_state, uint32_t n, ug_params p, int32_t n
     sa.n = n;
     sa.pval = p;
     sa.bounds_copies = kBoundsCopiesSingle;
-    int rc = run_steps(L.state, L.perm, sa, nsteps, max_boxes, L.fw, 128, 2, &L.saves, status, s);
+    int rc = run_steps(L.state, L.perm, sa, nsteps, max_boxes, L.fw, 128, 2, &L.saves, status, s,
+                       nullptr, windows_pay(n, max_boxes));
     if (rc != UG_OK) return rc;
     const float4 *W = reinterpret_cast<const float4 *>(grad_out);
     int nb = 0;

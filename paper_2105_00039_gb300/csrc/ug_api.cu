@@ -270,7 +270,8 @@ int ug_step(float *state, uint32_t *perm, uint32_t n, ug_params p, int32_t nstep
     sa.pval = p;
     sa.bounds_copies = bounds_copies(1);
     return run_steps(reinterpret_cast<float4 *>(state), perm, sa, nsteps, max_boxes, w, 128, 2,
-                     nullptr, status, static_cast<cudaStream_t>(stream));
+                     nullptr, status, static_cast<cudaStream_t>(stream), nullptr,
+                     windows_pay(n, max_boxes));
 }
 
 int ug_step_pairs_once(float *state, uint32_t *perm, uint32_t n, ug_params p, int32_t nsteps,
@@ -310,7 +311,7 @@ int ug_step_traced(float *state, uint32_t *perm, uint32_t n, ug_params p, int32_
     sa.bounds_copies = bounds_copies(1);
     return run_steps(reinterpret_cast<float4 *>(state), perm, sa, nsteps, max_boxes, w, 128, 2,
                      nullptr, status, static_cast<cudaStream_t>(stream),
-                     reinterpret_cast<cudaEvent_t const *>(events));
+                     reinterpret_cast<cudaEvent_t const *>(events), windows_pay(n, max_boxes));
 }
 
 int ug_step_batched(float *state, uint32_t *perm, const uint32_t *sim_offset, uint32_t nsims,
@@ -338,12 +339,13 @@ int ug_step_batched(float *state, uint32_t *perm, const uint32_t *sim_offset, ui
     if ((block != 64 && block != 128) || (apl != 1 && apl != 2) || (pair_mode != 0 && pair_mode != 1) ||
         walk < 0 || walk > 2)
         return UG_EINVAL;
-    sa.windows_always = walk == 2;
+
     if (pair_mode == 1)   // every pair once: its own kernels, whatever the sweep layout
         return run_steps(reinterpret_cast<float4 *>(state), perm, sa, nsteps, max_boxes, w, 128, 3,
                          nullptr, status, static_cast<cudaStream_t>(stream));
     return run_steps(reinterpret_cast<float4 *>(state), perm, sa, nsteps, max_boxes, w, block, apl,
-                     nullptr, status, static_cast<cudaStream_t>(stream), nullptr, walk != 1);
+                     nullptr, status, static_cast<cudaStream_t>(stream), nullptr,
+                     walk == 2 || (walk == 0 && windows_pay(n_total, max_boxes)));
 }
 
 int ug_tune_batched(const float *state, const uint32_t *sim_offset, uint32_t nsims, uint32_t n_total,

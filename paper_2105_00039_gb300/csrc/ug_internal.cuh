@@ -45,9 +45,9 @@ struct SimArgs {
     uint32_t bounds_copies;   // copies of the bounds accumulators (atomic spreading)
     bool per_box_table;       // the box table has one entry per box (a caller's table from
                               // ug_grid_build): kernels then ignore the geometry's sub-bins
-    bool windows_always;      // neighbour-row windows at every number of sub-bins per box
-                              // (default: only where they pay, see k_sweep2)
 };
+
+
 // A simulation's geometry as a kernel uses it (see SimArgs::per_box_table).
 __device__ __forceinline__ ug_grid_info sim_geo(const SimArgs &sa, const ug_grid_info *geo,
                                                 uint32_t s) {
@@ -193,6 +193,18 @@ __host__ __device__ __forceinline__ int sub_shift(uint32_t agents, unsigned long
 // Entries of a box table serving n agents in grids of at most max_boxes boxes.
 __host__ __device__ __forceinline__ unsigned long long table_capacity(uint32_t n, uint32_t max_boxes) {
     return (unsigned long long)max_boxes + n + (n >> 2) + 1;
+}
+// Neighbour-row windows pay where candidates dominate.  Measured on GB300
+// (4,194,304 cells): the windowed walk is 9% slower than the full runs at 8
+// neighbours per agent and 6% slower at 2, and 13% / 15% faster at 32 / 64.
+// The host cannot see a step's grid (it is built on the device), so it judges
+// from the agents and the box capacity: max_boxes bounds the boxes from above,
+// so the estimated sub-bins per box never exceed the grid's.  Windows are
+// used where that estimate reaches 8 sub-bins per box (6.4 agents per box or
+// more, about 16 neighbours per agent and up).  Either walk gives the same
+// bits, so a wrong guess costs time only.
+inline bool windows_pay(uint32_t n, uint32_t max_boxes) {
+    return sub_shift(n, max_boxes) >= 3;
 }
 __device__ __forceinline__ int grid_shift(const ug_grid_info &g) { return (int)g.reserved; }
 
@@ -730,10 +742,11 @@ void launch_sym_step(const float4 *sorted, const uint32_t *start, const ug_grid_
                      const SimArgs &sa, const SweepOut &out, unsigned long long *acc,
                      int32_t *status, cudaStream_t s, const uint32_t *skey);
 // Two agents per lane (ug_sweep2.cu), force or step mode: one simulation with
-// the windowed walk (windowed) or full neighbour runs, or many simulations.
+// the neighbour-row windows (windowed) or the full runs, or many simulations
+// (full runs).
 void launch_sweep2(int mode, const float4 *sorted, const uint32_t *start, const ug_grid_info *geo,
                    const SimArgs &sa, const SweepOut &out, int32_t *status, cudaStream_t s,
-                   const uint32_t *skey, bool windowed = true);
+                   const uint32_t *skey, bool windowed = false);
 void launch_apply(const float4 *st_in, const float4 *force, uint32_t n, const ug_params &p,
                   float4 *st_out, float4 *disp_out, int32_t *status, cudaStream_t s);
 
@@ -749,6 +762,6 @@ struct StepSaves {          // per-step records for the adjoint (nullable)
 int run_steps(float4 *state, uint32_t *perm, const SimArgs &sa, int nsteps, uint32_t max_boxes,
               const Workspace &w, int sweep_block, int agents_per_lane, const StepSaves *saves,
               int32_t *status, cudaStream_t s, cudaEvent_t const *events = nullptr,
-              bool windowed = true);
+              bool windowed = false);
 
 }  // namespace ug

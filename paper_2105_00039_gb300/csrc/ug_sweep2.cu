@@ -6,10 +6,9 @@
 // every candidate row is loaded once and tested against both agents, which
 // halves the per-candidate index, load and loop work of the one-agent-per-lane
 // sweep.  A lane whose two agents lie too far apart in box order to merge walks
-// the two 9-run sets one after the other.  In k_sweep2 with WIN (the fused
-// step's default for one simulation) each run of a grid with 8 x sub-bins per
-// box is cut to the agents' x-windows (see row_window); otherwise a run is the
-// row's three boxes.  Runs are walked in
+// the two 9-run sets one after the other.  k_sweep2<..., WIN> cuts each run to
+// the agents' x-windows (see row_window); without WIN a run is the row's three
+// boxes (the host picks, see windows_pay).  Runs are walked in
 // warp lockstep (k_sweep2 concatenates the three runs of each neighbour plane,
 // so the trip count is the warp's longest concatenation) with clamped indices
 // and masks; neighbouring lanes read the same candidate rows at the same time,
@@ -145,11 +144,6 @@ __device__ __forceinline__ bool mergeable(uint32_t k0, uint32_t k1, uint32_t dx,
 // S_i inflated by 2^-14, so no contact is ever outside its window.  A row with
 // w^2 <= 0 holds no candidate.  Contacts are met in the same order as over the
 // full runs (rows by (dz, dy), ascending slots), so the sums are the same bits.
-// Windows pay where candidates dominate: measured on GB300 (4M cells), they
-// cost more than they save at 2 and 8 neighbours per agent and save 12% at 32,
-// so a grid uses them when it has 8 sub-bins per box (6.4 agents per box or
-// more, about 16 neighbours and up); coarser grids walk the full runs.
-constexpr int kWindowShift = 3;
 constexpr float kWinInflate = 1.0f + 1.0f / 16384.0f;   // on S_i / e
 constexpr float kWinRootInflate = 1.0f + 1.0f / 1048576.0f;   // on the approximate root
 constexpr float kWinSlack = 1.0f / 1048576.0f;           // box units per box of extent
@@ -187,6 +181,46 @@ __device__ __forceinline__ bool row_window(const AgentBox &a, int dy, int dz, fl
     return lo <= hi;
 }
 
+// The three runs of neighbour plane dz cut to the served agents' windows (the
+// union of agent 0's and agent 1's where both are served): out[2r], out[2r+1]
+// are the first and the end slot of row dy = r - 1 (equal when it holds no
+// candidate).  Out of line, so that the full-run walk's registers are not
+// spent on it; the agents' boxes are recomputed from their rows.
+__device__ __noinline__ void plane_windows(float4 me0, float4 me1, bool s0, bool s1, uint32_t k0,
+                                           uint32_t k1, int dz, float o0, float o1, float o2,
+                                           float e, int d0, int d1, int d2, int ks, float margin,
+                                           const uint32_t *__restrict__ start, uint32_t *out) {
+    ug_grid_info g{};
+    g.origin[0] = o0; g.origin[1] = o1; g.origin[2] = o2;
+    g.edge = e;
+    g.dims[0] = d0; g.dims[1] = d1; g.dims[2] = d2;
+    const float inv_e = __frcp_rn(e);
+    const uint32_t K = 1u << ks, R = (uint32_t)d0 << ks;
+    const uint32_t plane = ((uint32_t)d0 * (uint32_t)d1) << ks;
+    const float slx = (float)(d0 + 2) * kWinSlack, sly = (float)(d1 + 2) * kWinSlack;
+    const float slz = (float)(d2 + 2) * kWinSlack;
+    const AgentBox a0 = agent_box(me0, g, inv_e, margin);
+    const AgentBox a1 = agent_box(me1, g, inv_e, margin);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const int dy = r - 1;
+        uint32_t wl = 0xffffffffu, wh = 0u;
+        auto take = [&](const AgentBox &a, uint32_t key) {
+            int l, h;
+            if (!row_window(a, dy, dz, sly, slz, slx, (float)K, (int)K, l, h)) return;
+            // the row's first table entry: the key's row shifted by (dy, dz)
+            const uint32_t rb = key + (uint32_t)dz * plane + (uint32_t)dy * R - ((uint32_t)a.bx << ks);
+            wl = min(wl, rb + (uint32_t)l);
+            wh = max(wh, rb + (uint32_t)h + 1u);
+        };
+        if (s0) take(a0, k0);
+        if (s1) take(a1, k1);
+        const bool any = wl < wh;
+        out[2 * r] = any ? __ldg(start + wl) : 0u;
+        out[2 * r + 1] = any ? __ldg(start + wh) : 0u;
+    }
+}
+
 template <int MODE, int T, bool WIN>
 __global__ void __launch_bounds__(T, 8)
 k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
@@ -211,26 +245,12 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     const uint32_t K = 1u << ks, R = dx << ks;                   // table entries per box, per row
     const uint32_t plane = ((uint32_t)g.dims[0] * (uint32_t)g.dims[1]) << ks;
     uint32_t k0 = 0, k1 = 0;
-    const bool win = WIN && (ks >= kWindowShift || sa.windows_always);   // uniform over the grid
-    AgentBox ab0{}, ab1{};   // win: the agents' places in the grid (the sort's own arithmetic)
-    const float inv_e = win ? __frcp_rn(g.edge) : 0.0f;
     if (v0) {
-        if (win) {
-            ab0 = agent_box(me0, g, inv_e, P.contact_margin);
-            ab1 = v1 ? agent_box(me1, g, inv_e, P.contact_margin) : ab0;
-            k0 = g.box_base + ((((uint32_t)ab0.bz * dimy + (uint32_t)ab0.by) * dx + (uint32_t)ab0.bx) << ks);
-            k1 = g.box_base + ((((uint32_t)ab1.bz * dimy + (uint32_t)ab1.by) * dx + (uint32_t)ab1.bx) << ks);
-        } else {
-            int bx, by, bz;
-            k0 = skey ? box_of_sort_key(__ldg(skey + i0), g) : box_key(me0, g, bx, by, bz);
-            k1 = k0;
-            if (v1) k1 = skey ? box_of_sort_key(__ldg(skey + i1), g) : box_key(me1, g, bx, by, bz);
-        }
+        int bx, by, bz;
+        k0 = skey ? box_of_sort_key(__ldg(skey + i0), g) : box_key(me0, g, bx, by, bz);
+        k1 = k0;
+        if (v1) k1 = skey ? box_of_sort_key(__ldg(skey + i1), g) : box_key(me1, g, bx, by, bz);
     }
-    const float slx = (float)(g.dims[0] + 2) * kWinSlack;
-    const float sly = (float)(g.dims[1] + 2) * kWinSlack;
-    const float slz = (float)(g.dims[2] + 2) * kWinSlack;
-    const float Kf = (float)K;
     const bool split = v1 && !mergeable(k0, k1, dx, ks);
     const bool exact_diffs =
         __all_sync(kFull, (!v0 || far_from_origin(me0, g.edge)) && (!v1 || far_from_origin(me1, g.edge)));
@@ -290,30 +310,11 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
             else if (gi < 3) { lo = k0; hi = k0; s0 = true; }
             else { lo = k1; hi = k1; s1 = true; }
             uint32_t a0, x0, a1, x1, a2, x2;
-            if (win) {
-                // each row's run cut to the union of the served agents' windows
-                // (table entries of the sub-bins that can hold their contacts)
-                uint32_t ab[3], xb[3];
-#pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    const int dy = r - 1;
-                    uint32_t wl = 0xffffffffu, wh = 0u;
-                    auto take = [&](const AgentBox &a, uint32_t key) {
-                        int l, h;
-                        if (!row_window(a, dy, dz, sly, slz, slx, Kf, (int)K, l, h)) return;
-                        // the row's first table entry: the key's row shifted by (dy, dz)
-                        const uint32_t rb = key + (uint32_t)dz * plane + (uint32_t)dy * R -
-                                            ((uint32_t)a.bx << ks);
-                        wl = min(wl, rb + (uint32_t)l);
-                        wh = max(wh, rb + (uint32_t)h + 1u);
-                    };
-                    if (s0) take(ab0, k0);
-                    if (s1) take(ab1, k1);
-                    const bool any = wl < wh;
-                    ab[r] = any ? __ldg(start + wl) : 0u;
-                    xb[r] = any ? __ldg(start + wh) : 0u;
-                }
-                a0 = ab[0]; x0 = xb[0]; a1 = ab[1]; x1 = xb[1]; a2 = ab[2]; x2 = xb[2];
+            if (WIN) {
+                uint32_t b6[6];
+                plane_windows(me0, me1, s0, s1, k0, k1, dz, g.origin[0], g.origin[1], g.origin[2],
+                              g.edge, g.dims[0], g.dims[1], g.dims[2], ks, P.contact_margin, start, b6);
+                a0 = b6[0]; x0 = b6[1]; a1 = b6[2]; x1 = b6[3]; a2 = b6[4]; x2 = b6[5];
             } else {
                 const uint32_t lz = lo + (uint32_t)dz * plane, hz = hi + (uint32_t)dz * plane;
                 a0 = __ldg(start + lz - R - K); x0 = __ldg(start + hz - R + 2u * K);
