@@ -23,14 +23,20 @@
 
 namespace ug {
 
-constexpr int kListCap2 = 16;   // candidates per agent between flushes
+// Candidates per agent between flushes: 24 in the one-simulation sweep (a
+// mean of 8 contacts then rarely needs a flush before the end of the walk),
+// 16 in the batched one.
+constexpr int kListCap1 = 24;
+constexpr int kListCap2 = 16;
 
-struct __align__(16) WarpLists2 {
-    uint32_t lst[2][kListCap2][32];
+template <int CAP>
+struct __align__(16) WarpListsT {
+    uint32_t lst[2][CAP][32];
 };
+using WarpLists1 = WarpListsT<kListCap1>;
+using WarpLists2 = WarpListsT<kListCap2>;
 static_assert(2 * sizeof(WarpLists2) >= sizeof(FinalizeScratch),
               "the epilogue reuses the lists of a CTA of 2 or more warps");
-constexpr uint32_t kWarpListWords = sizeof(WarpLists2) / 4;
 
 struct Accum {
     float sx, sy, sz, cx, cy, cz;
@@ -85,21 +91,24 @@ __device__ __forceinline__ void prefilter_pair(const float4 &q, const FilterPair
 
 // Exact contact test and Eq. 1 for the candidates listed since the last flush,
 // warp-converged (every lane calls it; trip count = the warp's longest list).
-// Out of line: the float-float contact test is long and runs a few times per
-// warp, so one copy of it serves every walk loop instead of one per loop.
-__device__ __noinline__ void flush_lists2(const float4 *__restrict__ st, const WarpLists2 *w,
-                                          int c0, int c1, float4 me0, float4 me1, float m2,
-                                          bool exact_diffs, ug_params P, Accum *a0, Accum *a1) {
+// Inlined, with the difference mode a template argument: the sums stay in
+// registers (a call would keep them in local memory).
+template <bool EXACT_DIFF>
+__device__ __forceinline__ void flush_lists1(const float4 *__restrict__ st, const WarpLists1 *w,
+                                             int c0, int c1, const float4 &me0, const float4 &me1,
+                                             float m2, const ug_params &P, Accum &a0, Accum &a1) {
     const int lane = threadIdx.x & 31;
     const int m0 = (int)__reduce_max_sync(kFull, (unsigned)c0);
     for (int k = 0; k < m0; ++k)
-        if (k < c0) add_contact(me0, __ldg(st + w->lst[0][k][lane]), m2, exact_diffs, P, *a0);
+        if (k < c0) add_contact(me0, __ldg(st + w->lst[0][k][lane]), m2, EXACT_DIFF, P, a0);
     const int m1 = (int)__reduce_max_sync(kFull, (unsigned)c1);
     for (int k = 0; k < m1; ++k)
-        if (k < c1) add_contact(me1, __ldg(st + w->lst[1][k][lane]), m2, exact_diffs, P, *a1);
+        if (k < c1) add_contact(me1, __ldg(st + w->lst[1][k][lane]), m2, EXACT_DIFF, P, a1);
 }
 
-// flush_lists2 for two agents that may belong to different simulations.
+// The same for the batched sweep, where the two agents may belong to different
+// simulations; out of line with the difference mode a run-time argument, so
+// that one copy of the long contact test serves its walk loops.
 __device__ __noinline__ void flush_lists2m(const float4 *__restrict__ st, const WarpLists2 *w,
                                            int c0, int c1, float4 me0, float4 me1, float m20,
                                            float m21, bool exact_diffs, ug_params P0,
@@ -221,16 +230,18 @@ __device__ __noinline__ void plane_windows(float4 me0, float4 me1, bool s0, bool
     }
 }
 
+// Six CTAs per SM: with 24-entry lists (24 KB a CTA of 128 threads) and the
+// inlined flush, fewer resident warps and a larger L1 beat eight.
 template <int MODE, int T, bool WIN>
-__global__ void __launch_bounds__(T, 8)
+__global__ void __launch_bounds__(T, 6)
 k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
          const ug_grid_info *__restrict__ geo, const uint32_t *__restrict__ skey, SimArgs sa,
          SweepOut out, int32_t *status) {
-    __shared__ WarpLists2 wl[T / 32];
+    __shared__ WarpLists1 wl[T / 32];
     chain_begin();
     if (cta_failed(status)) return;
     const int lane = threadIdx.x & 31;
-    WarpLists2 &w = wl[threadIdx.x >> 5];
+    WarpLists1 &w = wl[threadIdx.x >> 5];
     const uint32_t n = sa.n;
     const uint32_t i0 = (blockIdx.x * T + threadIdx.x) * 2u, i1 = i0 + 1u;
     const bool v0 = i0 < n, v1 = i1 < n;
@@ -255,11 +266,11 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     const bool exact_diffs =
         __all_sync(kFull, (!v0 || far_from_origin(me0, g.edge)) && (!v1 || far_from_origin(me1, g.edge)));
     const FilterPair fp = make_filter_pair(me0, me1, m2);
-    // the force sums are touched only by the flushes: kept in (local) memory
     Accum acc[2] = {{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u}, {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u}};
     int c0 = 0, c1 = 0;
     auto flush = [&]() {
-        flush_lists2(st, &w, c0, c1, me0, me1, m2, exact_diffs, P, &acc[0], &acc[1]);
+        if (exact_diffs) flush_lists1<true>(st, &w, c0, c1, me0, me1, m2, P, acc[0], acc[1]);
+        else flush_lists1<false>(st, &w, c0, c1, me0, me1, m2, P, acc[0], acc[1]);
         c0 = 0;
         c1 = 0;
     };
@@ -286,7 +297,7 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
                     ++c1;
                 }
             }
-            if (__any_sync(kFull, max(c0, c1) > kListCap2 - kWalkUnroll)) flush();
+            if (__any_sync(kFull, max(c0, c1) > kListCap1 - kWalkUnroll)) flush();
         }
     };
     // The 9 runs come as 3 neighbour planes (dz) of 3 runs (dy = -1, 0, +1),
@@ -371,7 +382,7 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     // each warp's 8 bounds words in its own lists, the last CTA's grid
     // finalisation across all of them
     accumulate_bounds_codes(sa, codes, v0, 0u, true, out.bounds, &wl[0].lst[0][0][0],
-                                kWarpListWords);
+                                sizeof(WarpLists1) / 4);
     if (elect_last_cta(&out.ctrl->done))
         finalize_grid(sa, out.bounds, out.geo_next, out.ctrl, out.max_boxes, status,
                       *reinterpret_cast<FinalizeScratch *>(wl));
@@ -509,7 +520,7 @@ k_sweep2m(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
 #pragma unroll
         for (int k = 0; k < 8; ++k) codes[k] = max(codes[k], c2[k]);
         accumulate_bounds_codes(sa, codes, v0, s0, true, out.bounds, &wl[0].lst[0][0][0],
-                                kWarpListWords);
+                                sizeof(WarpLists2) / 4);
     } else {
         accumulate_bounds_codes(sa, codes, v0, s0, false, out.bounds, nullptr, 0u);
         accumulate_bounds_codes(sa, c2, v1, s1, false, out.bounds, nullptr, 0u);
