@@ -492,7 +492,7 @@ def run_ours(args, world, rank, local, pg):
                      "step_hbm_frac": step_gbs / hbm},
         "kernel_us_per_step_traced": split,
         "kernel_share": {k: v / sum(split.values()) for k, v in split.items()},
-        "gpu_launches": args.steps * (2 + 5 * SIM_STEPS),
+        "gpu_launches": args.steps * (2 + 6 * SIM_STEPS),
         "clocks": clk.summary(),
         "wall_s_timed_region": wall,
     }

@@ -120,8 +120,8 @@ typedef struct {
     int32_t neighbour_walk;   /* with agents_per_lane 2 and pair_mode 0, one simulation:
                                  0 = each neighbour row cut to the x-window that can hold
                                  contacts where that pays, judged from n_total and
-                                 max_boxes (8 x sub-bins per box, about 16 neighbours per
-                                 agent and up), else the full three-box runs (default);
+                                 max_boxes (n_total >= 2.5 max_boxes, about 8 neighbours
+                                 per agent and up), else the full three-box runs (default);
                                  1 = always the full runs; 2 = always the windows.  The
                                  same bits every way.  Several simulations always walk
                                  full runs. */

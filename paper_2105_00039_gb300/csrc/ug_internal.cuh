@@ -199,12 +199,13 @@ __host__ __device__ __forceinline__ unsigned long long table_capacity(uint32_t n
 // neighbours per agent and 6% slower at 2, and 13% / 15% faster at 32 / 64.
 // The host cannot see a step's grid (it is built on the device), so it judges
 // from the agents and the box capacity: max_boxes bounds the boxes from above,
-// so the estimated sub-bins per box never exceed the grid's.  Windows are
-// used where that estimate reaches 8 sub-bins per box (6.4 agents per box or
-// more, about 16 neighbours per agent and up).  Either walk gives the same
-// bits, so a wrong guess costs time only.
+// so the agents per box it sees never exceed the grid's.  Windows are used
+// from 2.5 agents per box (2 or more sub-bins per box; measured on the
+// 4M-cell density cube: 2% slower than the full runs at 6 neighbours, 2.1
+// agents per box, 2% faster at 8, 7-20% faster from 12 up).  Either walk gives
+// the same bits, so a wrong guess costs time only.
 inline bool windows_pay(uint32_t n, uint32_t max_boxes) {
-    return sub_shift(n, max_boxes) >= 3;
+    return 2ull * n >= 5ull * max_boxes;
 }
 __device__ __forceinline__ int grid_shift(const ug_grid_info &g) { return (int)g.reserved; }
 

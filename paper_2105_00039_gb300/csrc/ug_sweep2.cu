@@ -193,23 +193,18 @@ __device__ __forceinline__ bool row_window(const AgentBox &a, int dy, int dz, fl
 // The three runs of neighbour plane dz cut to the served agents' windows (the
 // union of agent 0's and agent 1's where both are served): out[2r], out[2r+1]
 // are the first and the end slot of row dy = r - 1 (equal when it holds no
-// candidate).  Out of line, so that the full-run walk's registers are not
-// spent on it; the agents' boxes are recomputed from their rows.
-__device__ __noinline__ void plane_windows(float4 me0, float4 me1, bool s0, bool s1, uint32_t k0,
-                                           uint32_t k1, int dz, float o0, float o1, float o2,
-                                           float e, int d0, int d1, int d2, int ks, float margin,
+// candidate).  Out of line, so that the walk's registers are not spent on it;
+// the two agents' boxes (ab[0], ab[1]) are computed once per lane and kept in
+// local memory.
+__device__ __noinline__ void plane_windows(const AgentBox *ab, bool s0, bool s1, uint32_t k0,
+                                           uint32_t k1, int dz, int d0, int d1, int d2, int ks,
                                            const uint32_t *__restrict__ start, uint32_t *out) {
-    ug_grid_info g{};
-    g.origin[0] = o0; g.origin[1] = o1; g.origin[2] = o2;
-    g.edge = e;
-    g.dims[0] = d0; g.dims[1] = d1; g.dims[2] = d2;
-    const float inv_e = __frcp_rn(e);
     const uint32_t K = 1u << ks, R = (uint32_t)d0 << ks;
     const uint32_t plane = ((uint32_t)d0 * (uint32_t)d1) << ks;
     const float slx = (float)(d0 + 2) * kWinSlack, sly = (float)(d1 + 2) * kWinSlack;
     const float slz = (float)(d2 + 2) * kWinSlack;
-    const AgentBox a0 = agent_box(me0, g, inv_e, margin);
-    const AgentBox a1 = agent_box(me1, g, inv_e, margin);
+    const AgentBox a0 = ab[0];
+    const AgentBox a1 = ab[1];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
         const int dy = r - 1;
@@ -266,6 +261,12 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     const bool exact_diffs =
         __all_sync(kFull, (!v0 || far_from_origin(me0, g.edge)) && (!v1 || far_from_origin(me1, g.edge)));
     const FilterPair fp = make_filter_pair(me0, me1, m2);
+    AgentBox abox[2];
+    if (WIN) {
+        const float inv_e = __frcp_rn(g.edge);
+        abox[0] = agent_box(me0, g, inv_e, P.contact_margin);
+        abox[1] = agent_box(me1, g, inv_e, P.contact_margin);
+    }
     Accum acc[2] = {{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u}, {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u}};
     int c0 = 0, c1 = 0;
     auto flush = [&]() {
@@ -323,8 +324,8 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
             uint32_t a0, x0, a1, x1, a2, x2;
             if (WIN) {
                 uint32_t b6[6];
-                plane_windows(me0, me1, s0, s1, k0, k1, dz, g.origin[0], g.origin[1], g.origin[2],
-                              g.edge, g.dims[0], g.dims[1], g.dims[2], ks, P.contact_margin, start, b6);
+                plane_windows(abox, s0, s1, k0, k1, dz, g.dims[0], g.dims[1], g.dims[2], ks, start,
+                              b6);
                 a0 = b6[0]; x0 = b6[1]; a1 = b6[2]; x1 = b6[3]; a2 = b6[4]; x2 = b6[5];
             } else {
                 const uint32_t lz = lo + (uint32_t)dz * plane, hz = hi + (uint32_t)dz * plane;
@@ -381,11 +382,27 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     // the epilogue's scratch lives in the warps' list memory, no longer needed:
     // each warp's 8 bounds words in its own lists, the last CTA's grid
     // finalisation across all of them
-    accumulate_bounds_codes(sa, codes, v0, 0u, true, out.bounds, &wl[0].lst[0][0][0],
-                                sizeof(WarpLists1) / 4);
-    if (elect_last_cta(&out.ctrl->done))
-        finalize_grid(sa, out.bounds, out.geo_next, out.ctrl, out.max_boxes, status,
-                      *reinterpret_cast<FinalizeScratch *>(wl));
+    // each warp maximises its codes into one copy of the bounds accumulators
+    // (no CTA barrier: a warp that finishes early does not wait for the
+    // others); k_finalize1 turns them into the next grid
+    const uint32_t copy = (blockIdx.x * (T / 32) + (threadIdx.x >> 5)) % sa.bounds_copies;
+    uint32_t mine = 0u;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t m = __reduce_max_sync(kFull, codes[k]);
+        if (lane == k) mine = m;
+    }
+    if (lane < 8 && mine) atomicMax(&out.bounds[(size_t)copy * kBoundsWords + lane], mine);
+}
+
+// The next step's grid of one simulation from the bounds k_sweep2 accumulated
+// (one warp; finalize_grid is the code the other sweeps' last CTA runs).
+__global__ void __launch_bounds__(32)
+k_finalize1(SimArgs sa, uint32_t *bounds, ug_grid_info *geo, Ctrl *ctrl, uint32_t max_boxes,
+            int32_t *status) {
+    __shared__ FinalizeScratch fs;
+    chain_begin();
+    finalize_grid(sa, bounds, geo, ctrl, max_boxes, status, fs);
 }
 
 template <int MODE, int T, bool MULTI>
@@ -546,16 +563,22 @@ void launch_sweep2(int mode, const float4 *sorted, const uint32_t *start, const 
         if (mode == kSweepForce)
             launch_chained(k_sweep2<kSweepForce, T, true>, grid, T, s, sorted, start, geo, skey, sa,
                            out, status);
-        else
+        else {
             launch_chained(k_sweep2<kSweepStep, T, true>, grid, T, s, sorted, start, geo, skey, sa,
                            out, status);
+            launch_chained(k_finalize1, 1, 32, s, sa, out.bounds, out.geo_next, out.ctrl,
+                           out.max_boxes, status);
+        }
     } else {
         if (mode == kSweepForce)
             launch_chained(k_sweep2<kSweepForce, T, false>, grid, T, s, sorted, start, geo, skey, sa,
                            out, status);
-        else
+        else {
             launch_chained(k_sweep2<kSweepStep, T, false>, grid, T, s, sorted, start, geo, skey, sa,
                            out, status);
+            launch_chained(k_finalize1, 1, 32, s, sa, out.bounds, out.geo_next, out.ctrl,
+                           out.max_boxes, status);
+        }
     }
 }
 
