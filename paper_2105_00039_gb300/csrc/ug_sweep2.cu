@@ -396,8 +396,9 @@ k_sweep2(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
 }
 
 // The next step's grid of one simulation from the bounds k_sweep2 accumulated
-// (one warp; finalize_grid is the code the other sweeps' last CTA runs).
-__global__ void __launch_bounds__(32)
+// (finalize_grid is the code the other sweeps' last CTA runs).  256 threads:
+// one read of the kBoundsCopiesSingle x kBoundsWords accumulators each.
+__global__ void __launch_bounds__(256)
 k_finalize1(SimArgs sa, uint32_t *bounds, ug_grid_info *geo, Ctrl *ctrl, uint32_t max_boxes,
             int32_t *status) {
     __shared__ FinalizeScratch fs;
@@ -566,7 +567,7 @@ void launch_sweep2(int mode, const float4 *sorted, const uint32_t *start, const 
         else {
             launch_chained(k_sweep2<kSweepStep, T, true>, grid, T, s, sorted, start, geo, skey, sa,
                            out, status);
-            launch_chained(k_finalize1, 1, 32, s, sa, out.bounds, out.geo_next, out.ctrl,
+            launch_chained(k_finalize1, 1, 256, s, sa, out.bounds, out.geo_next, out.ctrl,
                            out.max_boxes, status);
         }
     } else {
@@ -576,7 +577,7 @@ void launch_sweep2(int mode, const float4 *sorted, const uint32_t *start, const 
         else {
             launch_chained(k_sweep2<kSweepStep, T, false>, grid, T, s, sorted, start, geo, skey, sa,
                            out, status);
-            launch_chained(k_finalize1, 1, 32, s, sa, out.bounds, out.geo_next, out.ctrl,
+            launch_chained(k_finalize1, 1, 256, s, sa, out.bounds, out.geo_next, out.ctrl,
                            out.max_boxes, status);
         }
     }
