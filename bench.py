@@ -185,15 +185,27 @@ class ClockSampler:
 def _oracle_chunk(args):
     """One process's share of a sampled oracle step: the population is rebuilt
     from its seed, the oracle's sampled step (its own kd-tree over all cells,
-    then the listed cells against every cell) is timed."""
-    n, nbar, seed, lo, hi, stride = args
+    then the listed cells against every cell) is timed.  With the GPU's forces
+    of the same cells (rows F_x, F_y, F_z, contacts, by cell index) it also
+    returns, after the timing, each cell's condition-scaled force error
+    |F_gpu - F| / max(|F|, S) (S: the sum of the pair terms' magnitudes) and
+    the number of cells whose contact count differs."""
+    n, nbar, seed, lo, hi, stride, gpu = args
     import oracle as O
     from paper_2105_00039_gb300 import populations as P
     st = P.density_cube(n, nbar, seed=seed)
     idx = np.arange(lo, hi, stride, dtype=np.int64)
     t0 = time.perf_counter()
-    O.step_sampled(st, idx, O.Params(max_disp=0.0))
-    return len(idx), time.perf_counter() - t0
+    ref = O.step_sampled(st, idx, O.Params(max_disp=0.0))
+    secs = time.perf_counter() - t0
+    if gpu is None:
+        return len(idx), secs, None
+    F, S = ref["F"], ref["S"]
+    scale = np.maximum(np.linalg.norm(F, axis=1), S)
+    diff = np.linalg.norm(gpu[:, :3].astype(np.float64) - F, axis=1)
+    err = np.where(scale > 0, diff / np.where(scale > 0, scale, 1.0), 0.0).astype(np.float32)
+    count_bad = int(np.sum(gpu[:, 3].astype(np.int64) != ref["npairs"]))
+    return len(idx), secs, (err, count_bad)
 
 
 class OraclePool:
@@ -206,14 +218,21 @@ class OraclePool:
         self.procs = procs
         self.pool = mp.get_context("spawn").Pool(procs) if procs > 1 else None
 
-    def step(self, n, nbar, seed, fraction=1.0):
+    def step(self, n, nbar, seed, fraction=1.0, gpu=None):
         """One sampled step over `fraction` of the cells (every cell when 1):
-        returns (cells evaluated, wall seconds of the slowest process)."""
+        returns (cells evaluated, wall seconds of the slowest process, and with
+        `gpu` (n x 4 float32, by cell index) the per-cell force errors and the
+        count of contact-count mismatches, else None)."""
         stride = max(1, int(round(1.0 / fraction)))
         per = (n + self.procs - 1) // self.procs
-        jobs = [(n, nbar, seed, p * per, min(n, (p + 1) * per), stride) for p in range(self.procs)]
+        jobs = [(n, nbar, seed, p * per, min(n, (p + 1) * per), stride,
+                 None if gpu is None else gpu[p * per:min(n, (p + 1) * per):stride])
+                for p in range(self.procs)]
         res = self.pool.map(_oracle_chunk, jobs) if self.pool else [_oracle_chunk(jobs[0])]
-        return sum(r[0] for r in res), max(r[1] for r in res)
+        cmp = None
+        if gpu is not None:
+            cmp = (np.concatenate([r[2][0] for r in res]), sum(r[2][1] for r in res))
+        return sum(r[0] for r in res), max(r[1] for r in res), cmp
 
     def close(self):
         if self.pool:
@@ -221,19 +240,31 @@ class OraclePool:
             self.pool.join()
 
 
-def cpu_oracle_baseline():
+def cpu_oracle_baseline(gpu_forces=None):
     """The oracle on all host cores (one full step of every cell, split over
-    the cores) and on one core (a sample of the cells, its kd-tree included)."""
+    the cores) and on one core (a sample of the cells, its kd-tree included).
+    With the GPU's forces of the same population it also returns the parity
+    of every cell's force and contact count against that oracle step (else
+    None in their place)."""
     cores = os.cpu_count() or 1
     pool = OraclePool(cores)
     try:
-        cells, secs = pool.step(N_AGENTS, MEAN_NEIGHBOURS, POP_SEED)
+        cells, secs, cmp = pool.step(N_AGENTS, MEAN_NEIGHBOURS, POP_SEED, gpu=gpu_forces)
     finally:
         pool.close()
+    parity = None
+    if cmp is not None:
+        err, count_bad = cmp
+        parity = {"workload": "the headline population's first step, every cell",
+                  "force_condition_scaled": {"max": float(err.max()),
+                                             "median": float(np.median(err)),
+                                             "cells": int(err.size), "tolerance": 1e-5},
+                  "contact_counts_differing": count_bad,
+                  "oracle": "FP64, kd-tree pair search (the same run as cpu_baseline)"}
     one = OraclePool(1)
-    cells1, secs1 = one.step(N_AGENTS, MEAN_NEIGHBOURS, POP_SEED, fraction=1.0 / 8.0)
+    cells1, secs1, _ = one.step(N_AGENTS, MEAN_NEIGHBOURS, POP_SEED, fraction=1.0 / 8.0)
     pinning = "none (the OS scheduler places the processes)"
-    return {"value": cells / secs, "unit": "agent-steps/s", "cores": cores, "kind": "oracle",
+    return parity, {"value": cells / secs, "unit": "agent-steps/s", "cores": cores, "kind": "oracle",
             "sample": f"one FP64 oracle step of all {cells} cells of the bench workload, split over "
                       f"{cores} spawned processes (each builds its own kd-tree over all cells); "
                       f"slowest process {secs:.1f} s",
@@ -254,7 +285,7 @@ def run_reference(args, world, rank, pg):
             pool.step(N_AGENTS, MEAN_NEIGHBOURS, POP_SEED, frac)
         cells, total = 0, 0.0
         for _ in range(args.steps):
-            c, dt = pool.step(N_AGENTS, MEAN_NEIGHBOURS, POP_SEED, frac)
+            c, dt, _ = pool.step(N_AGENTS, MEAN_NEIGHBOURS, POP_SEED, frac)
             cells += c
             total += dt
     finally:
@@ -294,6 +325,16 @@ def candidates_and_contacts(U, x, prm):
     cand = float((cnt * nb).sum().item() - n) / n
     F = U.compute_forces(srt, start, info, prm)
     return cand, float(F[:, 3].double().mean().item()), int(g["nboxes"])
+
+
+def forces_by_row(U, x, prm):
+    """The library's forces of every row of x (F_x, F_y, F_z, contacts), by row,
+    on the host."""
+    srt, perm, start, info, _ = U.grid_build(x, contact_margin=prm.contact_margin)
+    F = U.compute_forces(srt, start, info, prm)
+    out = np.empty((x.shape[0], 4), np.float32)
+    out[perm.cpu().numpy().astype(np.int64)] = F.cpu().numpy()
+    return out
 
 
 def _timed(fn, reps, flush=None):
@@ -459,6 +500,11 @@ def run_ours(args, world, rank, local, pg):
     # roofline of the dominant kernel (the sweep), per launch, and of the step
     avg_launch_ms = split["sweep"] / 1000.0
     cand, cont, boxes = candidates_and_contacts(U, pop.x0, prm)   # frozen population
+    # the GPU's forces of the population, compared with the oracle's step in the
+    # CPU baseline leg
+    gpu_forces = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        gpu_forces = forces_by_row(U, pop.x0, prm)
     alg_flops = n * (FLOPS_PER_CANDIDATE * cand + FLOPS_PER_CONTACT * cont + FLOPS_PER_AGENT)
     alu_tflops = alg_flops / (avg_launch_ms / 1000.0) / 1e12
     sweep_bytes = BYTES_PER_AGENT_SWEEP * n
@@ -542,7 +588,7 @@ def run_ours(args, world, rank, local, pg):
         line["pairs_once"] = measure_pairs_once(dev, flush)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_oracle_baseline()
+        line["parity"], line["cpu_baseline"] = cpu_oracle_baseline(gpu_forces)
         line["cpu_grid_baseline"] = cpu_grid_rate(st, 10)
     if rank == 0:
         print(json.dumps(line), flush=True)
