@@ -58,7 +58,7 @@ ISSUE_PEAK_GINST_S = 152 * 4 * 2.07
 # source as it was captured (sha256[:16] of the files below) and are reported
 # as null once that source changes.
 SWEEP_SOURCES = ("ug_sweep2.cu", "ug_internal.cuh")
-SWEEP_CAPTURE = {"src": "837d779f742fbc90", "dram_bytes": 95_002_624 + 38_718_720, "warp_inst": 594_229_723}
+SWEEP_CAPTURE = {"src": "ebfcc7f8904d28a8", "dram_bytes": 95_001_856 + 38_928_128, "warp_inst": 594_229_723}
 
 
 def sweep_source_hash() -> str:
@@ -732,7 +732,8 @@ def measure_batched(dev, flush, nsims=256, nsteps=50, reps=3):
             "bit_identical_to_plain": bool(same and same_graph),
             "tuned_sweep_block": int(tune.sweep_block),
             "tuned_agents_per_lane": int(tune.agents_per_lane),
-            "tuned_pair_mode": int(tune.pair_mode)}
+            "tuned_pair_mode": int(tune.pair_mode),
+            "tuned_neighbour_walk": int(tune.neighbour_walk)}
 
 
 def measure_adjoint(dev, flush, side=64, nsteps=50, ckpt=10, reps=3):

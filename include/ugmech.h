@@ -117,14 +117,16 @@ typedef struct {
     int32_t sweep_block;      /* 64 or 128; 0 = default (128) */
     int32_t agents_per_lane;  /* 1 or 2; 0 = default (2) */
     int32_t pair_mode;        /* 0 or 1; 0 = default */
-    int32_t neighbour_walk;   /* with agents_per_lane 2 and pair_mode 0, one simulation:
+    int32_t neighbour_walk;   /* with pair_mode 1 (any number of simulations), or with
+                                 agents_per_lane 2 and pair_mode 0 (one simulation):
                                  0 = each neighbour row cut to the x-window that can hold
                                  contacts where that pays, judged from n_total and
                                  max_boxes (n_total >= 2.5 max_boxes, about 8 neighbours
-                                 per agent and up), else the full three-box runs (default);
+                                 per agent and up; every pair once: n_total >= 8
+                                 max_boxes, about 24 and up), else the full three-box runs
+                                 (default);
                                  1 = always the full runs; 2 = always the windows.  The
-                                 same bits every way.  Several simulations always walk
-                                 full runs. */
+                                 same bits every way.  The other layouts walk full runs. */
     int32_t reserved[4];
 } ug_tuning;
 
@@ -223,10 +225,12 @@ int ug_step(float *state, uint32_t *perm, uint32_t n, ug_params p, int32_t nstep
  * atomics, so still deterministic), after which a second kernel moves the
  * agents.  Same arguments, workspace and results within the same tolerance as
  * ug_step, but not the same bits (fixed-point instead of compensated float32
- * sums).  It pays in dense grids: 1.7x at ~32 and 1.9x at ~64 neighbours per
- * agent on GB300, while on sparse grids (a few agents per box) the atomics cost
- * more than the halved walk saves and ug_step is faster.  For many simulations
- * use ug_step_batched with tuning->pair_mode = 1. */
+ * sums).  It pays in dense grids: 1.3x at ~32 and 1.5x at ~64 neighbours per
+ * agent on GB300 (from 8 agents per box of max_boxes its forward rows are cut
+ * to the agents' x-windows, with the same bits), while on sparse grids (a few
+ * agents per box) the atomics cost more than the halved walk saves and ug_step
+ * is faster.  For many simulations use ug_step_batched with
+ * tuning->pair_mode = 1. */
 int ug_step_pairs_once(float *state, uint32_t *perm, uint32_t n, ug_params p, int32_t nsteps,
                        uint32_t max_boxes, void *ws, size_t ws_bytes, int32_t *status, void *stream);
 
@@ -255,7 +259,9 @@ int ug_step_batched(float *state, uint32_t *perm, const uint32_t *sim_offset, ui
                     int32_t *status, void *stream);
 
 /* Time each candidate configuration (one agent per lane with 64 or 128 threads
- * per CTA, two agents per lane, every pair once) on the given batched problem -- three fused
+ * per CTA, two agents per lane, every pair once; the last two with the full
+ * runs and with the windows, the two-agent windows for one simulation only) on
+ * the given batched problem -- three fused
  * steps (grid build, sweep, move) of a scratch copy of the rows, after one
  * untimed step -- and write the fastest to *best (HOST pointer).  `state` is
  * only read.  Needs ws_bytes >= ug_workspace_bytes(n_total, nsims, max_boxes)

@@ -106,7 +106,7 @@ int run_steps(float4 *state, uint32_t *perm, const SimArgs &sa, int nsteps, uint
         o.ctrl = w.ctrl;
         o.max_boxes = max_boxes;
         if (agents_per_lane == 3)
-            launch_sym_step(sorted, start, w.geo, sa, o, w.acc, status, s, w.rank);
+            launch_sym_step(sorted, start, w.geo, sa, o, w.acc, status, s, w.rank, windowed);
         else if (agents_per_lane == 2)
             launch_sweep2(kSweepStep, sorted, start, w.geo, sa, o, status, s, w.rank, windowed);
         else
@@ -290,7 +290,8 @@ int ug_step_pairs_once(float *state, uint32_t *perm, uint32_t n, ug_params p, in
     sa.pval = p;
     sa.bounds_copies = bounds_copies(1);
     return run_steps(reinterpret_cast<float4 *>(state), perm, sa, nsteps, max_boxes, w, 128, 3,
-                     nullptr, status, static_cast<cudaStream_t>(stream));
+                     nullptr, status, static_cast<cudaStream_t>(stream), nullptr,
+                     windows_pay_pairs_once(n, max_boxes));
 }
 
 int ug_step_traced(float *state, uint32_t *perm, uint32_t n, ug_params p, int32_t nsteps,
@@ -342,7 +343,8 @@ int ug_step_batched(float *state, uint32_t *perm, const uint32_t *sim_offset, ui
 
     if (pair_mode == 1)   // every pair once: its own kernels, whatever the sweep layout
         return run_steps(reinterpret_cast<float4 *>(state), perm, sa, nsteps, max_boxes, w, 128, 3,
-                         nullptr, status, static_cast<cudaStream_t>(stream));
+                         nullptr, status, static_cast<cudaStream_t>(stream), nullptr,
+                         walk == 2 || (walk == 0 && windows_pay_pairs_once(n_total, max_boxes)));
     return run_steps(reinterpret_cast<float4 *>(state), perm, sa, nsteps, max_boxes, w, block, apl,
                      nullptr, status, static_cast<cudaStream_t>(stream), nullptr,
                      walk == 2 || (walk == 0 && windows_pay(n_total, max_boxes)));
@@ -389,22 +391,29 @@ int ug_tune_batched(const float *state, const uint32_t *sim_offset, uint32_t nsi
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return UG_ECUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return UG_ECUDA; }
-    // candidates: (agents per lane, threads per CTA), and every pair once (3),
-    // each timed on kTuneSteps fused steps (grid build + sweep + move) from the
-    // given rows, after one untimed step
+    // candidates: (agents per lane, threads per CTA, neighbour walk: 1 full runs,
+    // 2 windows), and every pair once (3), each timed on kTuneSteps fused steps
+    // (grid build + sweep + move) from the given rows, after one untimed step.
+    // The windows serve the two-agent sweep of one simulation and every pair
+    // once; the other layouts walk full runs.
     constexpr int kTuneSteps = 3;
-    const int cands[4][2] = {{1, 64}, {1, 128}, {2, 128}, {3, 128}};
+    constexpr int kCands = 6;
+    const int cands[kCands][3] = {{1, 64, 1}, {1, 128, 1}, {2, 128, 1}, {2, 128, 2}, {3, 128, 1},
+                                  {3, 128, 2}};
     float best_ms = 1e30f;
     int rc = UG_OK;
-    for (int c = 0; c < 4 && rc == UG_OK; ++c) {
+    for (int c = 0; c < kCands && rc == UG_OK; ++c) {
+        if (cands[c][0] == 2 && cands[c][2] == 2 && nsims > 1) continue;
+        const bool win = cands[c][2] == 2;
         rc = reset();
         if (rc == UG_OK)
-            rc = run_steps(rows, ids, sa, 1, max_boxes, w, cands[c][1], cands[c][0], nullptr, status, s);
+            rc = run_steps(rows, ids, sa, 1, max_boxes, w, cands[c][1], cands[c][0], nullptr, status, s,
+                           nullptr, win);
         if (rc == UG_OK) rc = reset();
         if (rc != UG_OK) break;
         cudaEventRecord(e0, s);
         rc = run_steps(rows, ids, sa, kTuneSteps, max_boxes, w, cands[c][1], cands[c][0], nullptr,
-                       status, s);
+                       status, s, nullptr, win);
         cudaEventRecord(e1, s);
         if (rc != UG_OK) break;
         if (cudaEventSynchronize(e1) != cudaSuccess) { rc = UG_ECUDA; break; }
@@ -415,6 +424,7 @@ int ug_tune_batched(const float *state, const uint32_t *sim_offset, uint32_t nsi
             best->pair_mode = cands[c][0] == 3 ? 1 : 0;
             best->agents_per_lane = cands[c][0] == 3 ? 2 : cands[c][0];
             best->sweep_block = cands[c][1];
+            best->neighbour_walk = cands[c][0] == 1 ? 0 : cands[c][2];
         }
     }
     int32_t hst = 0;

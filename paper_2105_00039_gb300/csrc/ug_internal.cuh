@@ -207,6 +207,13 @@ __host__ __device__ __forceinline__ unsigned long long table_capacity(uint32_t n
 inline bool windows_pay(uint32_t n, uint32_t max_boxes) {
     return 2ull * n >= 5ull * max_boxes;
 }
+// The same judgement for the every-pair-once walk, whose forward half-rows are
+// shorter and whose flush is cheaper, so the windows' set-up weighs more: from 8
+// agents per box (measured on the same cube: 2% slower at 8 neighbours, 2.8
+// agents per box; equal at 16; 2% faster at 32 and 6% at 64).
+inline bool windows_pay_pairs_once(uint32_t n, uint32_t max_boxes) {
+    return (unsigned long long)n >= 8ull * max_boxes;
+}
 __device__ __forceinline__ int grid_shift(const ug_grid_info &g) { return (int)g.reserved; }
 
 // Table entry of the first sub-bin of the agent's box (the box key); bx, by, bz
@@ -234,6 +241,59 @@ __device__ __forceinline__ uint32_t sort_key(const float4 &p, const ug_grid_info
 // The box key of a sort key.
 __device__ __forceinline__ uint32_t box_of_sort_key(uint32_t k, const ug_grid_info &g) {
     return k - ((k - g.box_base) & ((1u << grid_shift(g)) - 1u));
+}
+
+// ------------------------------------------------------------------ neighbour-row windows
+// With K = 2^ks table entries per box (x sub-bins, see sort_key) the three boxes
+// of a neighbour row are sorted by x at resolution e / K.  An agent's contacts
+// in row (dy, dz) lie within
+//   |x_j - x_i| < w,  w^2 = S_i^2 - g_y^2 - g_z^2,
+// where S_i >= r_i + r_j + 2m for every j (r_i + m + e / 2, as e >= d_max + 2m)
+// and g_y, g_z are the distances from the agent to that row's faces (0 for its
+// own row or plane), so the row's candidates are the sub-bins overlapping
+// [x_i - w, x_i + w]: two table reads give the window.  Everything is done in
+// box units, t = (p - o) / e exactly as the sort computes it, with slack for
+// its rounding (t carries at most 2^-23 relative error, so every window is
+// widened by (dims + 2) 2^-20 box units and the gaps narrowed by as much) and
+// S_i inflated by 2^-14, so no contact is ever outside its window.  A row with
+// w^2 <= 0 holds no candidate.  Contacts are met in the same order as over the
+// full runs (rows by (dz, dy), ascending slots), so the sums are the same bits.
+// The two-agent sweep (k_sweep2) and the every-pair-once walk (k_sym) use them.
+constexpr float kWinInflate = 1.0f + 1.0f / 16384.0f;   // on S_i / e
+constexpr float kWinRootInflate = 1.0f + 1.0f / 1048576.0f;   // on the approximate root
+constexpr float kWinSlack = 1.0f / 1048576.0f;           // box units per box of extent
+
+// An agent's place in the grid, in box units.
+struct AgentBox {
+    float tx, fy, fz;   // x position; fractional y and z positions in the box
+    float su;           // largest contact distance / e, inflated
+    int bx, by, bz;
+};
+__device__ __forceinline__ AgentBox agent_box(const float4 &p, const ug_grid_info &g, float inv_e,
+                                              float m) {
+    AgentBox a;
+    float ty, tz;
+    a.bx = box_coord(p.x, g.origin[0], g.edge, g.dims[0], &a.tx);
+    a.by = box_coord(p.y, g.origin[1], g.edge, g.dims[1], &ty);
+    a.bz = box_coord(p.z, g.origin[2], g.edge, g.dims[2], &tz);
+    a.fy = fminf(fmaxf(__fsub_rn(ty, (float)a.by), 0.0f), 1.0f);   // exact for rows of the grid
+    a.fz = fminf(fmaxf(__fsub_rn(tz, (float)a.bz), 0.0f), 1.0f);
+    a.su = (0.5f + (0.5f * p.w + m) * inv_e) * kWinInflate;
+    return a;
+}
+
+// Sub-bins [lo, hi] along the row (dy, dz) of the agent's box that can hold
+// its contacts; false when none can.
+__device__ __forceinline__ bool row_window(const AgentBox &a, int dy, int dz, float sly, float slz,
+                                           float slx, float Kf, int K, int &lo, int &hi) {
+    const float gy = dy == 0 ? 0.0f : fmaxf((dy < 0 ? a.fy : 1.0f - a.fy) - sly, 0.0f);
+    const float gz = dz == 0 ? 0.0f : fmaxf((dz < 0 ? a.fz : 1.0f - a.fz) - slz, 0.0f);
+    const float w2 = a.su * a.su - gy * gy - gz * gz;
+    if (!(w2 > 0.0f)) return false;
+    const float wx = w2 * rsqrtf(w2) * kWinRootInflate + slx;
+    lo = max((int)floorf((a.tx - wx) * Kf), (a.bx - 1) * K);
+    hi = min((int)floorf((a.tx + wx) * Kf), (a.bx + 1) * K + K - 1);
+    return lo <= hi;
 }
 
 // ------------------------------------------------------------------ float-float
@@ -741,7 +801,7 @@ void launch_sweep(int mode, const float4 *sorted, const uint32_t *start, const u
 // w.acc, then the move kernel (displacement, bounds, next grid) clears w.acc.
 void launch_sym_step(const float4 *sorted, const uint32_t *start, const ug_grid_info *geo,
                      const SimArgs &sa, const SweepOut &out, unsigned long long *acc,
-                     int32_t *status, cudaStream_t s, const uint32_t *skey);
+                     int32_t *status, cudaStream_t s, const uint32_t *skey, bool windowed);
 // Two agents per lane (ug_sweep2.cu), force or step mode: one simulation with
 // the neighbour-row windows (windowed) or the full runs, or many simulations
 // (full runs).

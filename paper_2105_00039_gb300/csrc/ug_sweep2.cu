@@ -138,58 +138,6 @@ __device__ __forceinline__ bool mergeable(uint32_t k0, uint32_t k1, uint32_t dx,
     return k1 >= k0 && ((k1 - k0) >> ks) + 3u <= dx;
 }
 
-// ------------------------------------------------------------------ neighbour-row windows
-// With K = 2^ks table entries per box (x sub-bins, see sort_key) the three boxes
-// of a neighbour row are sorted by x at resolution e / K.  An agent's contacts
-// in row (dy, dz) lie within
-//   |x_j - x_i| < w,  w^2 = S_i^2 - g_y^2 - g_z^2,
-// where S_i >= r_i + r_j + 2m for every j (r_i + m + e / 2, as e >= d_max + 2m)
-// and g_y, g_z are the distances from the agent to that row's faces (0 for its
-// own row or plane), so the row's candidates are the sub-bins overlapping
-// [x_i - w, x_i + w]: two table reads give the window.  Everything is done in
-// box units, t = (p - o) / e exactly as the sort computes it, with slack for
-// its rounding (t carries at most 2^-23 relative error, so every window is
-// widened by (dims + 2) 2^-20 box units and the gaps narrowed by as much) and
-// S_i inflated by 2^-14, so no contact is ever outside its window.  A row with
-// w^2 <= 0 holds no candidate.  Contacts are met in the same order as over the
-// full runs (rows by (dz, dy), ascending slots), so the sums are the same bits.
-constexpr float kWinInflate = 1.0f + 1.0f / 16384.0f;   // on S_i / e
-constexpr float kWinRootInflate = 1.0f + 1.0f / 1048576.0f;   // on the approximate root
-constexpr float kWinSlack = 1.0f / 1048576.0f;           // box units per box of extent
-
-// An agent's place in the grid, in box units.
-struct AgentBox {
-    float tx, fy, fz;   // x position; fractional y and z positions in the box
-    float su;           // largest contact distance / e, inflated
-    int bx, by, bz;
-};
-__device__ __forceinline__ AgentBox agent_box(const float4 &p, const ug_grid_info &g, float inv_e,
-                                              float m) {
-    AgentBox a;
-    float ty, tz;
-    a.bx = box_coord(p.x, g.origin[0], g.edge, g.dims[0], &a.tx);
-    a.by = box_coord(p.y, g.origin[1], g.edge, g.dims[1], &ty);
-    a.bz = box_coord(p.z, g.origin[2], g.edge, g.dims[2], &tz);
-    a.fy = fminf(fmaxf(__fsub_rn(ty, (float)a.by), 0.0f), 1.0f);   // exact for rows of the grid
-    a.fz = fminf(fmaxf(__fsub_rn(tz, (float)a.bz), 0.0f), 1.0f);
-    a.su = (0.5f + (0.5f * p.w + m) * inv_e) * kWinInflate;
-    return a;
-}
-
-// Sub-bins [lo, hi] along the row (dy, dz) of the agent's box that can hold
-// its contacts; false when none can.
-__device__ __forceinline__ bool row_window(const AgentBox &a, int dy, int dz, float sly, float slz,
-                                           float slx, float Kf, int K, int &lo, int &hi) {
-    const float gy = dy == 0 ? 0.0f : fmaxf((dy < 0 ? a.fy : 1.0f - a.fy) - sly, 0.0f);
-    const float gz = dz == 0 ? 0.0f : fmaxf((dz < 0 ? a.fz : 1.0f - a.fz) - slz, 0.0f);
-    const float w2 = a.su * a.su - gy * gy - gz * gz;
-    if (!(w2 > 0.0f)) return false;
-    const float wx = w2 * rsqrtf(w2) * kWinRootInflate + slx;
-    lo = max((int)floorf((a.tx - wx) * Kf), (a.bx - 1) * K);
-    hi = min((int)floorf((a.tx + wx) * Kf), (a.bx + 1) * K + K - 1);
-    return lo <= hi;
-}
-
 // The three runs of neighbour plane dz cut to the served agents' windows (the
 // union of agent 0's and agent 1's where both are served): out[2r], out[2r+1]
 // are the first and the end slot of row dy = r - 1 (equal when it holds no

@@ -11,7 +11,9 @@
 // false walks all 27 boxes and adds only to its own agent, which gives the
 // same bits (f_ji = -f_ij exactly in the float-float contact arithmetic, and
 // rounding to fixed point is symmetric): the comparison that isolates what
-// evaluating each pair once saves.
+// evaluating each pair once saves.  With WIN the four forward rows and the rest
+// of the own row are cut to the agent's x-window (row_window), which holds all
+// its contacts in that row, so the pairs found and the sums are the same.
 #include <cuda_runtime.h>
 
 #include "ug_internal.cuh"
@@ -35,7 +37,7 @@ struct SymList {
     uint32_t lst[kSymCap][32];
 };
 
-template <bool FORWARD, bool CHAINED>
+template <bool FORWARD, bool CHAINED, bool WIN>
 __global__ void __launch_bounds__(128)
 k_sym(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
       const ug_grid_info *__restrict__ geo, SimArgs sa,
@@ -68,6 +70,15 @@ k_sym(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     const uint32_t K = 1u << ks;
     const uint32_t row = (uint32_t)g.dims[0] << ks;
     const uint32_t plane = ((uint32_t)g.dims[0] * (uint32_t)g.dims[1]) << ks;
+    static_assert(FORWARD || !WIN, "the windows serve the forward walk");
+    AgentBox ab{};
+    float slx = 0.f, sly = 0.f, slz = 0.f;
+    if (WIN) {
+        ab = agent_box(me, g, __frcp_rn(g.edge), P.contact_margin);
+        slx = (float)(g.dims[0] + 2) * kWinSlack;
+        sly = (float)(g.dims[1] + 2) * kWinSlack;
+        slz = (float)(g.dims[2] + 2) * kWinSlack;
+    }
     long long sx = 0, sy = 0, sz = 0;
     uint32_t np = 0;
     bool overflow = false;
@@ -106,7 +117,20 @@ k_sym(const float4 *__restrict__ st, const uint32_t *__restrict__ start,
     for (int r = 0; r < kRuns; ++r) {
         uint32_t b = valid ? i : 0u;
         int len = 0;
-        if (valid) {
+        if (valid && WIN) {
+            // forward rows (dz, dy) = (1, -1), (1, 0), (1, 1), (0, 1), then the
+            // own row after i, each cut to the agent's x-window
+            const int dz = r < 3 ? 1 : 0;
+            const int dy = r < 3 ? r - 1 : (r == 3 ? 1 : 0);
+            int lo, hi;
+            if (row_window(ab, dy, dz, sly, slz, slx, (float)K, (int)K, lo, hi)) {
+                const uint32_t rb = key + (uint32_t)dz * plane + (uint32_t)dy * row -
+                                    ((uint32_t)ab.bx << ks);
+                b = r == 4 ? i + 1 : __ldg(start + rb + (uint32_t)lo);
+                len = (int)(__ldg(start + rb + (uint32_t)hi + 1u) - b);
+            }
+            if (len <= 0) { len = 0; b = i; }
+        } else if (valid) {
             if (FORWARD && r == 4) {
                 b = i + 1;
                 len = (int)(__ldg(start + key + 2u * K) - b);
@@ -212,10 +236,14 @@ k_sym_move(const float4 *__restrict__ st, unsigned long long *acc, SimArgs sa, S
 
 void launch_sym_step(const float4 *sorted, const uint32_t *start, const ug_grid_info *geo,
                      const SimArgs &sa, const SweepOut &out, unsigned long long *acc,
-                     int32_t *status, cudaStream_t s, const uint32_t *skey) {
+                     int32_t *status, cudaStream_t s, const uint32_t *skey, bool windowed) {
     const uint32_t n = sa.n;
-    launch_chained(k_sym<true, true>, (unsigned)((n + 127) / 128), 128u, s, sorted, start, geo, sa,
-                   acc, status, skey);
+    if (windowed)
+        launch_chained(k_sym<true, true, true>, (unsigned)((n + 127) / 128), 128u, s, sorted, start,
+                       geo, sa, acc, status, skey);
+    else
+        launch_chained(k_sym<true, true, false>, (unsigned)((n + 127) / 128), 128u, s, sorted, start,
+                       geo, sa, acc, status, skey);
     launch_chained(k_sym_move, (unsigned)((n + 255) / 256), 256u, s, sorted, acc, sa, out, status);
 }
 
@@ -231,9 +259,9 @@ int run_symmetric(bool forward, const float4 *sorted, const uint32_t *start, con
     sa.per_box_table = true;   // the caller's table from ug_grid_build
     const unsigned grid = (unsigned)((n + 127) / 128);
     if (forward)
-        k_sym<true, false><<<grid, 128, 0, s>>>(sorted, start, geo, sa, acc, status, nullptr);
+        k_sym<true, false, false><<<grid, 128, 0, s>>>(sorted, start, geo, sa, acc, status, nullptr);
     else
-        k_sym<false, false><<<grid, 128, 0, s>>>(sorted, start, geo, sa, acc, status, nullptr);
+        k_sym<false, false, false><<<grid, 128, 0, s>>>(sorted, start, geo, sa, acc, status, nullptr);
     k_sym_finish<<<(n + 255) / 256, 256, 0, s>>>(acc, n, force, status);
     return cudaGetLastError() == cudaSuccess ? UG_OK : UG_ECUDA;
 }

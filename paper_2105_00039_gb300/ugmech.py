@@ -599,8 +599,8 @@ def step_backward(ckpt_state, params: Params, nsteps: int, max_boxes: int, grad_
 
 
 def tune_batched(state, sim_offset, params_dev, nsims: int, max_boxes: int) -> ug_tuning:
-    """The fastest (sweep_block, agents_per_lane, pair_mode) for these
-    simulations, timed on scratch copies of the rows (state is only read)."""
+    """The fastest (sweep_block, agents_per_lane, pair_mode, neighbour_walk) for
+    these simulations, timed on scratch copies of the rows (state is only read)."""
     lib = load()
     _rows(state, "state")
     _batch(sim_offset, params_dev, nsims, state.device)

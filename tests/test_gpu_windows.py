@@ -11,7 +11,10 @@ ug_step does; the constants then come from device memory), and all must equal
 ug_step
 on populations whose grids use 1, 2, 4 and 8 x slices per box, at the edges of
 the method (a slab a few boxes thick, agents on box faces, everything near the
-origin, an odd agent count), and at full size.
+origin, an odd agent count), and at full size.  The every-pair-once step walks
+its forward rows through the same windows: its fixed-point sums do not depend
+on the order, so windows and full runs must give the same bits there too, for
+one simulation and for several.
 """
 import numpy as np
 import pytest
@@ -86,7 +89,7 @@ def test_windowed_walk_is_bit_identical_to_full_runs(U, name):
 
 @pytest.mark.parametrize("nbar", [8, 64])
 def test_windowed_walk_full_size(U, nbar):
-    """4,194,304 cells at a mean of 8 and 64 overlapping neighbours (4 and 8
+    """4,194,304 cells at a mean of 8 and 64 overlapping neighbours (2 and 8
     slices per box), two fused steps, as the density sweep runs them."""
     st = P.density_cube(1 << 22, float(nbar), seed=nbar)
     _same(U, st, U.Params(max_disp=0.0), nsteps=2, ways=("step", "batched_full_runs",
@@ -105,3 +108,61 @@ def test_per_box_entry_points_ignore_reserved(U):
     info2[44:48] = torch.tensor([3, 0, 0, 0], dtype=torch.uint8, device=DEV)
     F2 = U.compute_forces(srt, start, info2, U.Params())
     assert torch.equal(F, F2)
+
+
+def _run_pairs_once(U, st, prm, nsteps, walk, offs=None):
+    x = torch.from_numpy(np.ascontiguousarray(st, np.float32)).to(DEV)
+    n = x.shape[0]
+    if offs is None:
+        offs = np.array([0, n])
+    nsims = len(offs) - 1
+    parts = [x[int(offs[k]):int(offs[k + 1])] for k in range(nsims)]
+    mb = sum(U.estimate_max_boxes(p, prm.contact_margin, slack=2.0, extra_extent=8.0 * nsteps)
+             for p in parts)
+    sp = U.Stepper(n, mb, x.device, nsims=nsims)
+    perm = U.iota(n, x.device)
+    if walk == "step":
+        sp.step(x, perm, prm, nsteps, pairs_once=True)
+    else:
+        t = U.ug_tuning()
+        t.agents_per_lane, t.sweep_block, t.pair_mode = 2, 128, 1
+        t.neighbour_walk = {"full_runs": 1, "windows": 2, "default": 0}[walk]
+        o = torch.from_numpy(np.asarray(offs, np.int32)).to(DEV)
+        sp.step_batched(x, perm, o, torch.stack([prm.as_tensor(DEV)] * nsims), nsteps, t)
+    sp.check()
+    return x, perm
+
+
+@pytest.mark.parametrize("name", list(_cases()))
+def test_pairs_once_windows_are_bit_identical_to_full_runs(U, name):
+    st, margin = _cases()[name]
+    prm = U.Params(contact_margin=margin)
+    a, pa = _run_pairs_once(U, st, prm, 3, "step")
+    for how in ("full_runs", "windows", "default"):
+        b, pb = _run_pairs_once(U, st, prm, 3, how)
+        assert torch.equal(pa, pb), how
+        assert torch.equal(a, b), how
+
+
+def test_pairs_once_windows_several_simulations(U):
+    """Three simulations of 1, 2 and 8 x slices per box in one batched call:
+    windows and full runs give the same bits."""
+    sts = [P.density_cube(6000, 2.0, seed=11), P.density_cube(9000, 16.0, seed=12),
+           P.density_cube(7001, 40.0, seed=13)]
+    st = np.concatenate(sts)
+    offs = np.cumsum([0] + [len(t) for t in sts])
+    prm = U.Params()
+    a, pa = _run_pairs_once(U, st, prm, 3, "full_runs", offs)
+    b, pb = _run_pairs_once(U, st, prm, 3, "windows", offs)
+    assert torch.equal(pa, pb)
+    assert torch.equal(a, b)
+
+
+def test_pairs_once_windows_full_size(U):
+    """4,194,304 cells at a mean of 64 overlapping neighbours, two steps."""
+    st = P.density_cube(1 << 22, 64.0, seed=64)
+    prm = U.Params(max_disp=0.0)
+    a, pa = _run_pairs_once(U, st, prm, 2, "full_runs")
+    b, pb = _run_pairs_once(U, st, prm, 2, "windows")
+    assert torch.equal(pa, pb)
+    assert torch.equal(a, b)
