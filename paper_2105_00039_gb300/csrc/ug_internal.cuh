@@ -399,6 +399,101 @@ __device__ __forceinline__ bool far_from_origin(const float4 &a, float e) {
     return fabsf(a.x) >= lim && fabsf(a.y) >= lim && fabsf(a.z) >= lim;
 }
 
+// ------------------------------------------------------------------ FP32x2 pairs
+// The exact contact test and Eq. 1 of two pairs at once, in Blackwell's FP32x2
+// instructions (the two-agent sweep: entry k of each of the lane's two agents'
+// lists).  Every packed
+// operation rounds each half as the scalar one does, and the sequence is
+// contact_t's and eq1_coef's, so the results are the same bits (the two-agent
+// sweep is tested against the batched sweep's scalar flush).  Two rules keep it
+// so: the compiler may fuse a packed multiply into a packed add that consumes
+// it, so every rounded product that feeds an add or a subtraction is formed with
+// scalar __fmul_rn (never fused); and where a half holds no candidate, or no
+// contact, the two-agent sweep adds an exact zero (cz = 0), which leaves a
+// compensated sum and its error term unchanged (a running sum that starts at +0
+// never becomes -0).
+__device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a product that an add or a subtraction consumes (see above)
+__device__ __forceinline__ float2 mul2_unfused(float2 a, float2 b) {
+    return pk(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y));
+}
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &e) {
+    s = add2(a, b);
+    const float2 bp = sub2(s, a);
+    const float2 ap = sub2(s, bp);
+    e = add2(sub2(a, ap), sub2(b, bp));
+}
+__device__ __forceinline__ void two_prod2(float2 a, float2 b, float2 &p, float2 &e) {
+    p = mul2_unfused(a, b);
+    e = fma2(a, b, neg2(p));
+}
+
+// The exact contact test (contact_t) and Eq. 1 (eq1_coef) of two pairs at once,
+// (a0, b0) and (a1, b1), as the two halves of FP32x2 operations, bit for bit as
+// the scalar functions compute them.  a* are given as packed x, y, z and radius;
+// h0, h1 say which halves hold a listed candidate.  Returns the contact flags
+// and, for contacts, the force coefficient (coef * (p_a - p_b) is the force on
+// a) and p_a - p_b.  DIFFS_EXACT: the float32 centre differences are exact
+// (far_from_origin), else they are formed with TwoSum.
+template <bool DIFFS_EXACT>
+__device__ __forceinline__ void contact_eq1_x2(float2 ax, float2 ay, float2 az, float2 ra,
+                                               const float4 &q0, const float4 &q1, bool h0, bool h1,
+                                               float m2, float2 kk, float2 gg, float2 &hx,
+                                               float2 &hy, float2 &hz, float2 &coef, bool &t0,
+                                               bool &t1) {
+    const float2 bx = pk(q0.x, q1.x), by = pk(q0.y, q1.y), bz = pk(q0.z, q1.z);
+    float2 lx = pk(0.f, 0.f), ly = pk(0.f, 0.f), lz = pk(0.f, 0.f);
+    if (DIFFS_EXACT) {
+        hx = sub2(ax, bx);
+        hy = sub2(ay, by);
+        hz = sub2(az, bz);
+    } else {
+        two_sum2(ax, neg2(bx), hx, lx);
+        two_sum2(ay, neg2(by), hy, ly);
+        two_sum2(az, neg2(bz), hz, lz);
+    }
+    float2 px, ex, py, ey, pz, ez;
+    two_prod2(hx, hx, px, ex);
+    two_prod2(hy, hy, py, ey);
+    two_prod2(hz, hz, pz, ez);
+    float2 s1, e1, D, e2;
+    two_sum2(px, py, s1, e1);
+    two_sum2(s1, pz, D, e2);
+    float2 E = add2(add2(add2(add2(ex, ey), ez), e1), e2);
+    if (!DIFFS_EXACT)
+        E = fma2(pk(2.0f, 2.0f), fma2(hx, lx, fma2(hy, ly, mul2(hz, lz))), E);
+    const float2 rb = mul2(pk(0.5f, 0.5f), pk(q0.w, q1.w));   // exact
+    float2 sh, sl;
+    two_sum2(ra, rb, sh, sl);
+    const float2 rsum = sh;
+    if (m2 != 0.0f) {
+        float2 t, te;
+        two_sum2(sh, pk(m2, m2), t, te);
+        sh = t;
+        sl = add2(sl, te);
+    }
+    float2 S2, S2e;
+    two_prod2(sh, sh, S2, S2e);
+    S2e = fma2(mul2(pk(2.0f, 2.0f), sh), sl, S2e);            // 2 sh: exact
+    const float2 q = add2(sub2(S2, D), sub2(S2e, E));
+    t0 = h0 && q.x > 0.0f && D.x > 0.0f;
+    t1 = h1 && q.y > 0.0f && D.y > 0.0f;
+    const float2 invd = pk(rsqrtf(D.x), rsqrtf(D.y));
+    const float2 den = add2(sh, mul2_unfused(D, invd));
+    const float2 delta = pk(__fdividef(q.x, den.x), __fdividef(q.y, den.y));
+    const float2 rr = mul2(ra, rb);
+    const float2 R = pk(__fdividef(rr.x, rsum.x), __fdividef(rr.y, rsum.y));
+    const float2 rd = mul2(R, delta);
+    const float2 root = pk(__fmul_rn(rd.x, rsqrtf(rd.x)), __fmul_rn(rd.y, rsqrtf(rd.y)));
+    const float2 phi = fma2(kk, delta, neg2(mul2(gg, root)));
+    coef = mul2(phi, invd);
+}
+
 // ------------------------------------------------------------------ neighbour traversal
 // With boxes numbered x-fastest the 27 boxes around box key k are 9 runs of 3
 // consecutive boxes, one per (dy, dz): with K table entries per box, row

@@ -89,39 +89,6 @@ __device__ __forceinline__ void prefilter_pair(const float4 &q, const FilterPair
     p1 = d2.y < s2.y;
 }
 
-// ------------------------------------------------------------------ packed flush
-// The exact contact test and Eq. 1 of add_contact for both agents of a lane at
-// once, in Blackwell's FP32x2 instructions: entry k of agent 0's list and entry k
-// of agent 1's list form the two halves of each packed operand.  Every packed
-// operation rounds each half as the scalar one does, and the sequence is
-// add_contact's, so the sums are the same bits (tested against the batched
-// sweep's scalar flush).  Two rules keep it so: the compiler may fuse a packed
-// multiply into a packed add that consumes it, so every rounded product that
-// feeds an add or a subtraction is formed with scalar __fmul_rn (never fused);
-// and a lane without an entry k, or whose entry is no contact, adds an exact
-// zero (cz = 0), which leaves a compensated sum and its error term unchanged
-// (a running sum that starts at +0 never becomes -0).
-__device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-// a product that an add or a subtraction consumes (see above)
-__device__ __forceinline__ float2 mul2_unfused(float2 a, float2 b) {
-    return pk(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y));
-}
-__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &e) {
-    s = add2(a, b);
-    const float2 bp = sub2(s, a);
-    const float2 ap = sub2(s, bp);
-    e = add2(sub2(a, ap), sub2(b, bp));
-}
-__device__ __forceinline__ void two_prod2(float2 a, float2 b, float2 &p, float2 &e) {
-    p = mul2_unfused(a, b);
-    e = fma2(a, b, neg2(p));
-}
-
 // Exact contact test and Eq. 1 for the candidates listed since the last flush,
 // warp-converged (every lane calls it; trip count = the warp's longest list,
 // both agents' entries k in one pass).  DIFFS_EXACT: the warp's float32 centre
@@ -142,54 +109,10 @@ __device__ __forceinline__ void flush_lists1(const float4 *__restrict__ st, cons
         const bool h0 = k < c0, h1 = k < c1;
         const float4 q0 = __ldg(st + (h0 ? w->lst[0][k][lane] : 0u));   // row 0: a row that exists
         const float4 q1 = __ldg(st + (h1 ? w->lst[1][k][lane] : 0u));
-        const float2 bx = pk(q0.x, q1.x), by = pk(q0.y, q1.y), bz = pk(q0.z, q1.z);
-        // contact_t, both halves
-        float2 hx, hy, hz, lx = pk(0.f, 0.f), ly = pk(0.f, 0.f), lz = pk(0.f, 0.f);
-        if (DIFFS_EXACT) {
-            hx = sub2(ax, bx);
-            hy = sub2(ay, by);
-            hz = sub2(az, bz);
-        } else {
-            two_sum2(ax, neg2(bx), hx, lx);
-            two_sum2(ay, neg2(by), hy, ly);
-            two_sum2(az, neg2(bz), hz, lz);
-        }
-        float2 px, ex, py, ey, pz, ez;
-        two_prod2(hx, hx, px, ex);
-        two_prod2(hy, hy, py, ey);
-        two_prod2(hz, hz, pz, ez);
-        float2 s1, e1, D, e2;
-        two_sum2(px, py, s1, e1);
-        two_sum2(s1, pz, D, e2);
-        float2 E = add2(add2(add2(add2(ex, ey), ez), e1), e2);
-        if (!DIFFS_EXACT)
-            E = fma2(pk(2.0f, 2.0f), fma2(hx, lx, fma2(hy, ly, mul2(hz, lz))), E);
-        const float2 rb = mul2(pk(0.5f, 0.5f), pk(q0.w, q1.w));   // exact
-        float2 sh, sl;
-        two_sum2(ra, rb, sh, sl);
-        const float2 rsum = sh;
-        if (m2 != 0.0f) {
-            float2 t, te;
-            two_sum2(sh, pk(m2, m2), t, te);
-            sh = t;
-            sl = add2(sl, te);
-        }
-        float2 S2, S2e;
-        two_prod2(sh, sh, S2, S2e);
-        S2e = fma2(mul2(pk(2.0f, 2.0f), sh), sl, S2e);            // 2 sh: exact
-        const float2 q = add2(sub2(S2, D), sub2(S2e, E));
-        const bool t0 = h0 && q.x > 0.0f && D.x > 0.0f;
-        const bool t1 = h1 && q.y > 0.0f && D.y > 0.0f;
-        const float2 invd = pk(rsqrtf(D.x), rsqrtf(D.y));
-        const float2 den = add2(sh, mul2_unfused(D, invd));
-        const float2 delta = pk(__fdividef(q.x, den.x), __fdividef(q.y, den.y));
-        // eq1_coef, both halves
-        const float2 rr = mul2(ra, rb);
-        const float2 R = pk(__fdividef(rr.x, rsum.x), __fdividef(rr.y, rsum.y));
-        const float2 rd = mul2(R, delta);
-        const float2 root = pk(__fmul_rn(rd.x, rsqrtf(rd.x)), __fmul_rn(rd.y, rsqrtf(rd.y)));
-        const float2 phi = fma2(kk, delta, neg2(mul2(gg, root)));
-        const float2 coef = mul2(phi, invd);
+        float2 hx, hy, hz, coef;
+        bool t0, t1;
+        contact_eq1_x2<DIFFS_EXACT>(ax, ay, az, ra, q0, q1, h0, h1, m2, kk, gg, hx, hy, hz, coef,
+                                    t0, t1);
         const float2 cz = pk(t0 ? coef.x : 0.0f, t1 ? coef.y : 0.0f);
         float2 t, e;
         two_sum2(SX, mul2_unfused(cz, hx), t, e); SX = t; CX = add2(CX, e);
