@@ -225,7 +225,7 @@ int ug_step(float *state, uint32_t *perm, uint32_t n, ug_params p, int32_t nstep
  * atomics, so still deterministic), after which a second kernel moves the
  * agents.  Same arguments, workspace and results within the same tolerance as
  * ug_step, but not the same bits (fixed-point instead of compensated float32
- * sums).  It pays in dense grids: 1.3x at ~32 and 1.5x at ~64 neighbours per
+ * sums).  It pays in dense grids: 1.2x at ~32 and 1.4x at ~64 neighbours per
  * agent on GB300 (from 8 agents per box of max_boxes its forward rows are cut
  * to the agents' x-windows, with the same bits), while on sparse grids (a few
  * agents per box) the atomics cost more than the halved walk saves and ug_step

@@ -14,7 +14,9 @@
 // and masks; neighbouring lanes read the same candidate rows at the same time,
 // which the L1 serves once.  Candidates that pass the packed float32
 // pre-filter go to per-agent lists, and the exact float-float contact test and
-// Eq. 1 run in warp-converged batches.  k_sweep2 serves one simulation;
+// Eq. 1 run in warp-converged batches (in k_sweep2 both agents' k-th entries in
+// one FP32x2 pass, contact_eq1_x2).  k_sweep2 serves one simulation and leaves
+// the next grid to k_finalize1;
 // k_sweep2m serves many (a lane whose agents belong to different simulations
 // walks them separately, each with its own simulation's grid and constants).
 #include <cuda_runtime.h>
