@@ -4,6 +4,7 @@ clock/throttle samples that decide whether a run is kept."""
 import os
 import sys
 
+import numpy as np
 import pytest
 import torch
 import torch.distributed as dist
@@ -129,3 +130,28 @@ def test_issue_roofline(monkeypatch):
     assert abs(r["frac"] - r["achieved_ginst_s"] / (152 * 4 * 2.07)) < 1e-12
     monkeypatch.setattr(bench, "SWEEP_CAPTURE", dict(cap, src="0" * 16))
     assert bench.issue_roofline(0.1) is None
+
+
+def test_parity_leg_compares_every_cell():
+    """The CPU baseline leg's parity block: the oracle's own forces rounded to
+    float32 stand in for the GPU's (error at float32 rounding), one planted
+    contact-count mismatch is counted, and every cell is compared."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle as O
+    from paper_2105_00039_gb300 import populations as P
+    n, nbar, seed = 1500, 8.0, 8
+    st = P.density_cube(n, nbar, seed=seed)
+    ref = O.step_sampled(st, np.arange(n), O.Params(max_disp=0.0))
+    fake = np.concatenate([ref["F"].astype(np.float32),
+                           ref["npairs"][:, None].astype(np.float32)], axis=1)
+    fake[7, 3] += 1.0
+    pool = bench.OraclePool(2)
+    try:
+        cells, secs, cmp = pool.step(n, nbar, seed, gpu=fake)
+    finally:
+        pool.close()
+    err, count_bad = cmp
+    assert cells == n and err.size == n and secs > 0
+    assert count_bad == 1
+    assert 0.0 < float(err.max()) < 1e-6
