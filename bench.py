@@ -58,7 +58,7 @@ ISSUE_PEAK_GINST_S = 152 * 4 * 2.07
 # source as it was captured (sha256[:16] of the files below) and are reported
 # as null once that source changes.
 SWEEP_SOURCES = ("ug_sweep2.cu", "ug_internal.cuh")
-SWEEP_CAPTURE = {"src": "a27ff2a618475dcb", "dram_bytes": 95_006_208 + 38_871_808, "warp_inst": 575_849_854}
+SWEEP_CAPTURE = {"src": "88518fcd5b8d6723", "dram_bytes": 95_005_440 + 38_936_832, "warp_inst": 575_849_854}
 
 
 def sweep_source_hash() -> str:

@@ -121,7 +121,7 @@ typedef struct {
                                  agents_per_lane 2 and pair_mode 0 (one simulation):
                                  0 = each neighbour row cut to the x-window that can hold
                                  contacts where that pays, judged from n_total and
-                                 max_boxes (n_total >= 2.5 max_boxes, about 8 neighbours
+                                 max_boxes (n_total >= 2 max_boxes, about 6 neighbours
                                  per agent and up; every pair once: n_total >= 8
                                  max_boxes, about 24 and up), else the full three-box runs
                                  (default);

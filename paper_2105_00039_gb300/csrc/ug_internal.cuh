@@ -200,12 +200,12 @@ __host__ __device__ __forceinline__ unsigned long long table_capacity(uint32_t n
 // The host cannot see a step's grid (it is built on the device), so it judges
 // from the agents and the box capacity: max_boxes bounds the boxes from above,
 // so the agents per box it sees never exceed the grid's.  Windows are used
-// from 2.5 agents per box (2 or more sub-bins per box; measured on the
-// 4M-cell density cube: 2% slower than the full runs at 6 neighbours, 2.1
-// agents per box, 2% faster at 8, 7-20% faster from 12 up).  Either walk gives
+// from 2 agents per box (measured on the 4M-cell density cube: equal to the
+// full runs at 5 neighbours, 1.7 agents per box; 1.5% faster at 6, 2.1 agents
+// per box; 3% at 7, 5% at 8, 10% at 10, 23-26% at 32-64).  Either walk gives
 // the same bits, so a wrong guess costs time only.
 inline bool windows_pay(uint32_t n, uint32_t max_boxes) {
-    return 2ull * n >= 5ull * max_boxes;
+    return (unsigned long long)n >= 2ull * max_boxes;
 }
 // The same judgement for the every-pair-once walk, whose forward half-rows are
 // shorter and whose flush is cheaper, so the windows' set-up weighs more: from 8
